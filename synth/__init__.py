@@ -1,0 +1,85 @@
+"""Seeded synthetic inputs shared by the oracle checks and the CUDA engine's tests.
+
+This module only draws random numbers and assembles inputs; it contains none
+of the method's arithmetic (no decomposition, stitching or tree logic).
+
+Series: a piecewise Tucker tensor time series of shape T x D_2 x ... x D_p,
+standing in for the paper's 3-way datasets (Section 8.1; the datasets are not
+used).  Each regime of ``regime`` slices draws, in this order from one
+``numpy.random.Generator(PCG64(seed))``: a core with N(0,1) entries of shape
+r_1 x ... x r_p, a temporal factor (Q of a Gaussian l x r_1 matrix), and
+non-temporal factors (Q of Gaussian D_n x r_n matrices); the regime's slab is
+core x_1 A x_2 B ... (the generator's own einsum), scaled so that the signal
+has unit RMS per entry (``unit_signal``) unless ``literal_scale`` is set.
+Finally i.i.d. N(0, sigma^2) noise is added, slab by slab, from the same
+generator.
+
+Query ranges: "uniform" draws two distinct integers of {0..T}, sorted, read
+as the half-open range [a, b); "loguniform" draws L = round(exp(U[ln lo,
+ln hi])) and t_s uniformly from {0..T-L}.
+"""
+import string
+
+import numpy as np
+
+
+def _orthonormal(rng, m, r):
+    Q, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    return Q[:, :r]
+
+
+def piecewise_tucker(T, dims, ranks, regime, sigma, seed, literal_scale=False, dtype=np.float64):
+    """Seeded piecewise-Tucker series (see module docstring)."""
+    dims = tuple(int(d) for d in dims)
+    ranks = tuple(int(r) for r in ranks)
+    p = len(ranks)
+    assert len(dims) == p - 1
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    X = np.empty((int(T),) + dims, dtype=np.float64)
+    letters = string.ascii_lowercase
+    core_idx = letters[:p]
+    out_idx = letters[13:13 + p]
+    for start in range(0, int(T), int(regime)):
+        l = min(int(regime), int(T) - start)
+        rr = [min(ranks[0], l)] + [min(r, d) for r, d in zip(ranks[1:], dims)]
+        core = rng.standard_normal(tuple(rr))
+        if not literal_scale:
+            core *= np.sqrt(l * np.prod(dims) / np.prod(rr))
+        facs = [_orthonormal(rng, l, rr[0])] + [_orthonormal(rng, d, r) for d, r in zip(dims, rr[1:])]
+        spec = core_idx + "," + ",".join(out_idx[n] + core_idx[n] for n in range(p)) + "->" + out_idx
+        X[start:start + l] = np.einsum(spec, core, *facs, optimize=True)
+    for start in range(0, int(T), int(regime)):
+        l = min(int(regime), int(T) - start)
+        X[start:start + l] += sigma * rng.standard_normal((l,) + dims)
+    return X.astype(dtype, copy=False)
+
+
+def query_ranges(T, n, seed, kind="uniform", lo=16, hi=None):
+    """n seeded query ranges [t_s, t_e) over a series of length T."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    T = int(T)
+    out = np.empty((int(n), 2), dtype=np.int64)
+    for i in range(int(n)):
+        if kind == "uniform":
+            a, b = rng.choice(T + 1, size=2, replace=False)
+            out[i] = (min(a, b), max(a, b))
+        elif kind == "loguniform":
+            top = T if hi is None else min(int(hi), T)
+            L = int(round(np.exp(rng.uniform(np.log(lo), np.log(top)))))
+            L = max(1, min(L, T))
+            ts = int(rng.integers(0, T - L + 1))
+            out[i] = (ts, ts + L)
+        else:
+            raise ValueError(kind)
+    return out
+
+
+# Workloads with the shapes of the paper's 3-way series (Section 8.1) and the
+# configurations the benchmark and the parity tests run.
+WORKLOADS = {
+    "fp64_small": dict(T=256, dims=(30, 20), ranks=(5, 5, 5), regime=64, sigma=0.01, B=4,
+                       n_queries=100, kind="uniform", seed=1001, qseed=2001, dtype="f64"),
+    "fp32_plain": dict(T=4096, dims=(100, 100), ranks=(10, 10, 10), regime=512, sigma=0.05, B=16,
+                       n_queries=1000, kind="loguniform", lo=16, hi=4096, seed=1002, qseed=2002,
+                       dtype="f32"),
+}
