@@ -1,0 +1,160 @@
+/*
+ * tucket.h -- C ABI of the GB300 engine for range queries of Tucker
+ * decomposition over a stream segment tree (TUCKET, arXiv 2501.06647).
+ *
+ * Problem (Section 3 of the paper): a tensor stream X of shape
+ * T x D_2 x ... x D_p grows by one slice X_T (D_2 x ... x D_p) per stream
+ * update; a range query [t_s, t_e) asks for a Tucker decomposition
+ * G x_1 U1 ... x_p Up of the subtensor X[t_s:t_e), with G of shape
+ * r_1 x ... x r_p, U1 of shape (t_e - t_s) x r_1 and Un of shape D_n x r_n.
+ *
+ * Conventions shared by every call:
+ *  - Mode 0 is time (the paper's mode 1).  Tensors are dense, row-major
+ *    (C order), which is the paper's vec ordering (Appendix A).
+ *  - Element type is the tree's dtype: double (TK_F64) or float (TK_F32).
+ *  - Time ranges are half open, 0 <= t_s < t_e <= T.
+ *  - Pointers are device pointers unless the call's `io` argument is
+ *    TK_IO_HOST, in which case the data pointers are host pointers and the
+ *    library copies through its own device staging buffers.
+ *  - The caller owns every buffer it passes; the library owns the tree's
+ *    device arena and workspaces.  Inputs are consumed before the call's
+ *    stream work completes; the library never keeps a caller pointer.
+ *  - Calls are asynchronous on the tree's stream unless stated otherwise;
+ *    tk_sync() waits and reports device-side errors.
+ *  - Every function returns TK_OK (0) or a negative tk_status; a call that
+ *    fails argument validation changes nothing.  No exception crosses the ABI.
+ *  - One tree must not be used from two host threads at once.
+ */
+#ifndef TUCKET_H
+#define TUCKET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TK_MAX_MODES 6
+
+typedef enum tk_status {
+  TK_OK = 0,
+  TK_ERR_ARG = -1,         /* malformed argument (null pointer, bad config) */
+  TK_ERR_RANGE = -2,       /* time range outside [0, T) or empty */
+  TK_ERR_RANK = -3,        /* query rank < 1 or above the build rank */
+  TK_ERR_NOMEM = -4,       /* device allocation failed */
+  TK_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+  TK_ERR_STATE = -6,       /* call not valid in the tree's current state */
+  TK_ERR_WORKSPACE = -7,   /* device job exceeded its workspace (reported by tk_sync) */
+  TK_ERR_TOO_BIG = -8      /* request exceeds a fixed limit of the engine */
+} tk_status;
+
+typedef enum tk_dtype { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
+typedef enum tk_io { TK_IO_DEVICE = 0, TK_IO_HOST = 1 } tk_io;
+
+/* Tree configuration.  Hyperparameter defaults follow Section 8.1 of the
+ * paper: at most 20 ALS iterations, tolerance 0.01, theta = 0.7. */
+typedef struct tk_config {
+  int32_t p;                        /* number of modes, 2..TK_MAX_MODES */
+  int64_t dims[TK_MAX_MODES];       /* dims[1..p-1] = D_2..D_p; dims[0] unused */
+  int32_t ranks[TK_MAX_MODES];      /* build ranks r_1..r_p (>= 1) */
+  int32_t leaf_slices;              /* B: slices per leaf block (>= 1; 1 = paper) */
+  int32_t theta_num, theta_den;     /* pruning threshold theta = num/den in (0,1] */
+  int32_t max_iter;                 /* ALS iteration cap for leaves and stitches */
+  double tol;                       /* stop when |e_k - e_{k-1}| < tol; <= 0: run max_iter */
+  int32_t dtype;                    /* tk_dtype */
+  int32_t device;                   /* CUDA device ordinal */
+} tk_config;
+
+/* One node of a hit set (Algorithm 1, Section 5.1), in time order. */
+typedef struct tk_hit {
+  int32_t level;                    /* 0 = leaf block; level j spans 2^j blocks */
+  int32_t partial;                  /* 1 if the node is not contained in the query */
+  int64_t index;                    /* node index within its level */
+  int64_t node_lo, node_hi;         /* node range [sigma, tau) in slices */
+  int64_t lo, hi;                   /* clipped range [max(t_s,sigma), min(t_e,tau)) */
+} tk_hit;
+
+/* Per-query report. */
+typedef struct tk_query_info {
+  int32_t ranks[TK_MAX_MODES];      /* effective output ranks (<= requested) */
+  int32_t iters;                    /* ALS iterations run; < 0 on a device-side error */
+  int32_t n_hits;                   /* hit-set size s */
+  double fit_err;                   /* sqrt(1 - ||G||^2 / ||Y~||^2) of the stitched tensor */
+} tk_query_info;
+
+typedef struct tk_tree tk_tree;
+
+/* Fill *cfg with defaults: p = 3, ranks 10, B = 1, theta = 7/10,
+ * max_iter = 20, tol = 0.01, TK_F32, device 0.  dims must still be set. */
+int tk_config_default(tk_config* cfg);
+
+/* Create an empty tree (T = 0) on cfg->device.  cuda_stream is a
+ * cudaStream_t to run on, or NULL for a stream the tree creates and owns. */
+int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out);
+void tk_tree_destroy(tk_tree* t);
+
+/* Build the tree over X (T x D_2 x ... x D_p) on an EMPTY tree.  The result
+ * is the tree that T successive tk_stream_append calls produce (Section 4.2,
+ * Algorithms 3-4): leaf blocks are decomposed by Tucker-ALS (Section 2) and
+ * every complete intermediate node by Stitch (Algorithm 2) of its children. */
+int tk_tree_build(tk_tree* t, const void* X, int64_t T, int io);
+
+/* Stream update (Section 3, Algorithm 4): append one slice.  When a leaf
+ * block completes, the leaf is decomposed and the nu_2(#blocks) newly
+ * complete ancestors are re-decomposed by Stitch of their two children. */
+int tk_stream_append(tk_tree* t, const void* slice, int io);
+
+int64_t tk_timespan(const tk_tree* t);
+
+/* Pruned hit set of [t_s, t_e) (Algorithm 1), written to host array out.
+ * Synchronous.  *n_out receives the hit count; TK_ERR_TOO_BIG if > cap. */
+int tk_hit_set(tk_tree* t, int64_t t_s, int64_t t_e, tk_hit* out, int cap, int* n_out);
+
+/* Elements of one query's packed output for ranks r (NULL = build ranks):
+ *   prod_n r_n  (core, r_1 x ... x r_p)
+ * + (t_e - t_s) * r_1  (U1, row-major)
+ * + sum_{n>=2} D_n * r_n  (Un, row-major).
+ * Entries beyond the effective ranks are zero.  Returns < 0 on error. */
+int64_t tk_query_output_elems(const tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks);
+
+/* Range query of Tucker decomposition (Section 6.1): Recall, partial-hit
+ * approximation (Eq. partial-tucker), Stitch (Algorithm 2).  `out` holds
+ * tk_query_output_elems() elements.  ranks = NULL means the build ranks.
+ * If info != NULL (host pointer) the call is synchronous and fills it. */
+int tk_range_query(tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks,
+                   void* out, tk_query_info* info, int io);
+
+/* Batched range queries: n independent queries in one persistent launch.
+ * ranges: 2n int64 (t_s, t_e pairs); offsets: n+1 int64 element offsets of
+ * each query's packed output in `out` (tk_batch_layout computes them).
+ * With io = TK_IO_DEVICE, ranges/offsets/out are device pointers and the
+ * call is asynchronous; with TK_IO_HOST they are host pointers and the call
+ * copies in, computes, copies out and synchronizes.  info: optional host
+ * array of n reports (makes the call synchronous). */
+int tk_batch_layout(const tk_tree* t, int n, const int64_t* ranges_host,
+                    const int32_t* ranks, int64_t* offsets_host);
+int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t* offsets,
+                         const int32_t* ranks, void* out, tk_query_info* info, int io);
+
+/* Copy a stored node's decomposition to host memory, packed like a query
+ * output with the build ranks and the node's full time range (for tests).
+ * ranks_out (TK_MAX_MODES) receives the node's ranks.  Synchronous. */
+int tk_node_payload(tk_tree* t, int level, int64_t index, void* out_host,
+                    int64_t out_elems, int32_t* ranks_out);
+
+/* Device bytes held by the tree's node arena (cores, factors, temporal rows). */
+int64_t tk_arena_bytes(const tk_tree* t);
+
+/* Wait for the tree's stream; return the first device-side error, if any. */
+int tk_sync(tk_tree* t);
+
+/* Kernel launches issued by this tree since creation (all engine kernels). */
+int64_t tk_launch_count(const tk_tree* t);
+
+const char* tk_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKET_H */

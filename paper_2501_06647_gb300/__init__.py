@@ -1,0 +1,279 @@
+"""Python binding of the GB300 range-query Tucker engine (TUCKET, arXiv 2501.06647).
+
+Argument marshalling only: every step of tree build, stream update and range
+query runs in the CUDA kernels of ``libtucket.so`` (built in-tree by
+``build.py``) behind the C ABI of ``include/tucket.h``.  PyTorch is used for
+device buffers and streams.  There is no CPU fallback: if the library is
+missing, importing ``lib()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtucket.so")
+MAX_MODES = 6
+
+TK_F64, TK_F32 = 0, 1
+TK_IO_DEVICE, TK_IO_HOST = 0, 1
+
+_ERR = {
+    -1: "invalid argument", -2: "time range outside [0, T) or empty", -3: "query rank out of bounds",
+    -4: "device allocation failed", -5: "CUDA runtime error", -6: "invalid tree state",
+    -7: "device job exceeded its workspace", -8: "request exceeds an engine limit",
+}
+
+
+class TkConfig(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("dims", ctypes.c_int64 * MAX_MODES),
+                ("ranks", ctypes.c_int32 * MAX_MODES), ("leaf_slices", ctypes.c_int32),
+                ("theta_num", ctypes.c_int32), ("theta_den", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("dtype", ctypes.c_int32),
+                ("device", ctypes.c_int32)]
+
+
+class TkHit(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("partial", ctypes.c_int32), ("index", ctypes.c_int64),
+                ("node_lo", ctypes.c_int64), ("node_hi", ctypes.c_int64), ("lo", ctypes.c_int64),
+                ("hi", ctypes.c_int64)]
+
+
+class TkQueryInfo(ctypes.Structure):
+    _fields_ = [("ranks", ctypes.c_int32 * MAX_MODES), ("iters", ctypes.c_int32),
+                ("n_hits", ctypes.c_int32), ("fit_err", ctypes.c_double)]
+
+
+# Every symbol the header declares, with its ctypes signature.
+_SIGS = {
+    "tk_config_default": (ctypes.c_int, [ctypes.POINTER(TkConfig)]),
+    "tk_tree_create": (ctypes.c_int, [ctypes.POINTER(TkConfig), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "tk_tree_destroy": (None, [ctypes.c_void_p]),
+    "tk_tree_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]),
+    "tk_stream_append": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tk_timespan": (ctypes.c_int64, [ctypes.c_void_p]),
+    "tk_hit_set": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(TkHit),
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "tk_query_output_elems": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]),
+    "tk_range_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.POINTER(TkQueryInfo), ctypes.c_int]),
+    "tk_batch_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "tk_range_query_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tk_node_payload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_void_p]),
+    "tk_arena_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "tk_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "tk_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "tk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib_handle = None
+
+
+def lib():
+    """Load libtucket.so from the source tree (raises if it was not built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2501_06647_gb300/build.py (no CPU fallback)")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib_handle = h
+    return _lib_handle
+
+
+class TuckerError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {_ERR.get(code, 'error')} ({code})")
+        self.code = code
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise TuckerError(rc, what)
+
+
+def _np_dtype(dtype):
+    return np.float64 if dtype == "f64" else np.float32
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    assert x.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+class Tree:
+    """A stream segment tree on one GPU (Section 4.2 of the paper).
+
+    dims are the non-temporal sizes D_2..D_p, ranks the build ranks r_1..r_p,
+    leaf_slices the slices per leaf block, theta the pruning threshold as a
+    fraction (num, den), dtype "f64" or "f32".
+    """
+
+    def __init__(self, dims, ranks, leaf_slices=1, theta=(7, 10), max_iter=20, tol=0.01, dtype="f32",
+                 device=0, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.ranks = tuple(int(r) for r in ranks)
+        self.p = len(self.ranks)
+        if len(self.dims) != self.p - 1:
+            raise ValueError("need len(dims) == len(ranks) - 1")
+        self.dtype = dtype
+        self.np_dtype = _np_dtype(dtype)
+        cfg = TkConfig()
+        lib().tk_config_default(ctypes.byref(cfg))
+        cfg.p = self.p
+        for n, d in enumerate(self.dims):
+            cfg.dims[n + 1] = d
+        for n, r in enumerate(self.ranks):
+            cfg.ranks[n] = r
+        cfg.leaf_slices = int(leaf_slices)
+        cfg.theta_num, cfg.theta_den = int(theta[0]), int(theta[1])
+        cfg.max_iter = int(max_iter)
+        cfg.tol = float(tol)
+        cfg.dtype = TK_F64 if dtype == "f64" else TK_F32
+        cfg.device = int(device)
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
+        _check(lib().tk_tree_create(ctypes.byref(cfg), s, ctypes.byref(h)), "tk_tree_create")
+        self.h = h
+        self.B = int(leaf_slices)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tk_tree_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- updates ---------------------------------------------------------
+    def build(self, X):
+        """tree_build over X (T x D_2 x ... ; torch CUDA tensor or host numpy array)."""
+        io = TK_IO_DEVICE if hasattr(X, "is_cuda") and X.is_cuda else TK_IO_HOST
+        if io == TK_IO_HOST:
+            X = np.ascontiguousarray(X, dtype=self.np_dtype)
+        _check(lib().tk_tree_build(self.h, _ptr(X), int(X.shape[0]), io), "tk_tree_build")
+
+    def append(self, X_T):
+        """stream update with one slice (torch CUDA tensor or host numpy array)."""
+        io = TK_IO_DEVICE if hasattr(X_T, "is_cuda") and X_T.is_cuda else TK_IO_HOST
+        if io == TK_IO_HOST:
+            X_T = np.ascontiguousarray(X_T, dtype=self.np_dtype)
+        _check(lib().tk_stream_append(self.h, _ptr(X_T), io), "tk_stream_append")
+
+    @property
+    def T(self):
+        return int(lib().tk_timespan(self.h))
+
+    def sync(self):
+        _check(lib().tk_sync(self.h), "tk_sync")
+
+    def launch_count(self):
+        return int(lib().tk_launch_count(self.h))
+
+    def arena_bytes(self):
+        return int(lib().tk_arena_bytes(self.h))
+
+    # ---- queries ---------------------------------------------------------
+    def hit_set(self, ts, te):
+        """Algorithm 1's hit set as (level, index, node_lo, node_hi, lo, hi, partial) tuples."""
+        cap = 64
+        arr = (TkHit * cap)()
+        n = ctypes.c_int()
+        _check(lib().tk_hit_set(self.h, int(ts), int(te), arr, cap, ctypes.byref(n)), "tk_hit_set")
+        return [(h.level, h.index, h.node_lo, h.node_hi, h.lo, h.hi, h.partial) for h in arr[: n.value]]
+
+    def _ranks_arg(self, ranks):
+        if ranks is None:
+            return None, self.ranks
+        arr = (ctypes.c_int32 * MAX_MODES)(*([int(r) for r in ranks] + [1] * (MAX_MODES - len(ranks))))
+        return arr, tuple(int(r) for r in ranks)
+
+    def unpack(self, flat, L, ranks=None):
+        """Split one packed query output into (G, [U1, U2, ...]) views."""
+        rq = self.ranks if ranks is None else tuple(ranks)
+        c = int(np.prod(rq))
+        G = flat[:c].reshape(rq)
+        off = c
+        U = [flat[off:off + L * rq[0]].reshape(L, rq[0])]
+        off += L * rq[0]
+        for n in range(1, self.p):
+            U.append(flat[off:off + self.dims[n - 1] * rq[n]].reshape(self.dims[n - 1], rq[n]))
+            off += self.dims[n - 1] * rq[n]
+        return G, U
+
+    def query(self, ts, te, ranks=None):
+        """Range query through the C ABI with host buffers: returns (G, U, info)."""
+        rarr, rq = self._ranks_arg(ranks)
+        n = int(lib().tk_query_output_elems(self.h, int(ts), int(te), rarr))
+        if n < 0:
+            _check(n, "tk_query_output_elems")
+        out = np.zeros(n, dtype=self.np_dtype)
+        info = TkQueryInfo()
+        _check(lib().tk_range_query(self.h, int(ts), int(te), rarr, _ptr(out), ctypes.byref(info), TK_IO_HOST),
+               "tk_range_query")
+        G, U = self.unpack(out, int(te) - int(ts), rq)
+        r = list(info.ranks[: self.p])
+        G = G[tuple(slice(0, x) for x in r)]
+        U = [u[:, :x] for u, x in zip(U, r)]
+        return G, U, dict(ranks=r, iters=info.iters, n_hits=info.n_hits, fit_err=info.fit_err)
+
+    def layout(self, ranges, ranks=None):
+        ranges = np.ascontiguousarray(ranges, dtype=np.int64).reshape(-1, 2)
+        rarr, _ = self._ranks_arg(ranks)
+        offs = np.zeros(len(ranges) + 1, dtype=np.int64)
+        _check(lib().tk_batch_layout(self.h, len(ranges), _ptr(ranges), rarr, _ptr(offs)), "tk_batch_layout")
+        return offs
+
+    def query_batch(self, ranges, offsets, out, ranks=None, info=None):
+        """Batched range queries, all buffers on the device (asynchronous).
+
+        ranges: int64 tensor (n, 2); offsets: int64 tensor (n+1); out: tensor
+        of offsets[-1] elements of the tree's dtype.  info: optional host
+        array of TkQueryInfo (makes the call synchronous).
+        """
+        rarr, _ = self._ranks_arg(ranks)
+        n = int(ranges.shape[0])
+        ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
+        _check(lib().tk_range_query_batch(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), ip,
+                                          TK_IO_DEVICE), "tk_range_query_batch")
+
+    def query_batch_host(self, ranges, offsets=None, out=None, ranks=None, with_info=True):
+        """Batched range queries through the C ABI with HOST buffers (copies inside the call)."""
+        ranges = np.ascontiguousarray(ranges, dtype=np.int64).reshape(-1, 2)
+        if offsets is None:
+            offsets = self.layout(ranges, ranks)
+        if out is None:
+            out = np.zeros(int(offsets[-1]), dtype=self.np_dtype)
+        rarr, _ = self._ranks_arg(ranks)
+        info = (TkQueryInfo * len(ranges))() if with_info else None
+        ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
+        _check(lib().tk_range_query_batch(self.h, len(ranges), _ptr(ranges), _ptr(offsets), rarr, _ptr(out), ip,
+                                          TK_IO_HOST), "tk_range_query_batch")
+        return out, offsets, info
+
+    def node_payload(self, level, index):
+        """A stored node's (H, [V1, V2, ...], ranks), trimmed to its logical ranks."""
+        B = self.B
+        lo = (int(index) << int(level)) * B
+        hi = min(lo + (1 << int(level)) * B, self.T)
+        n = int(lib().tk_query_output_elems(self.h, 0, hi - lo, None))
+        out = np.zeros(n, dtype=self.np_dtype)
+        rk = (ctypes.c_int32 * MAX_MODES)()
+        _check(lib().tk_node_payload(self.h, int(level), int(index), _ptr(out), n, rk), "tk_node_payload")
+        G, U = self.unpack(out, hi - lo)
+        r = list(rk[: self.p])
+        return G[tuple(slice(0, x) for x in r)], [u[:, :x] for u, x in zip(U, r)], r

@@ -1,0 +1,780 @@
+// Host side of the engine: the C ABI of include/tucket.h, the tree metadata,
+// the pooled HBM arena, the workspaces, and the launch sequences of tree
+// build (Section 4.2), stream update (Algorithms 3-4) and range query
+// (Section 6.1).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "tk_internal.h"
+
+namespace {
+
+int64_t next_pow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+int ceil_log2(int64_t x) {
+  int h = 0;
+  while (((int64_t)1 << h) < x) ++h;
+  return h;
+}
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tk_tree {
+  tk_config cfg{};
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t es = 4;
+  int p = 0;
+  int64_t slice_elems = 0;
+  // state
+  int64_t T = 0, nb = 0;
+  bool tail_dirty = false;
+  // arena capacity
+  int64_t nbcap = 0;
+  int nlevels = 0;
+  int64_t level_base[TK_MAXL] = {};
+  int64_t nslots = 0;
+  int64_t core_stride = 0;
+  int64_t fac_stride[TK_MAXP] = {};
+  DevBuf core_pool, fac_pool[TK_MAXP], tfac, node_ranks, tail_raw;
+  // workspaces
+  DevBuf ws_stitch, ws_leaf, status;
+  int64_t ws_stitch_per_cta = 0, ws_leaf_per_cta = 0;
+  int ws_stitch_ctas = 0, ws_leaf_ctas = 0;
+  int nsm_stitch = 0, nsm_leaf = 0;
+  int sm_count = 0;
+  // staging for host io and batch metadata
+  DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf;
+  int64_t launches = 0;
+};
+
+namespace {
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? TK_OK : TK_ERR_CUDA; }
+
+int dalloc(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.ptr) return TK_OK;
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return TK_OK;
+  if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.ptr = nullptr;
+    return TK_ERR_NOMEM;
+  }
+  b.bytes = bytes;
+  return TK_OK;
+}
+
+void dfree(DevBuf& b) {
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int64_t nbt_of(const tk_tree* t) { return (t->T + t->cfg.leaf_slices - 1) / t->cfg.leaf_slices; }
+
+TkTreeView make_view(const tk_tree* t) {
+  TkTreeView v{};
+  v.p = t->p;
+  for (int n = 0; n < TK_MAXP; ++n) {
+    v.D[n] = n < t->p ? (int)t->cfg.dims[n] : 1;
+    v.r[n] = n < t->p ? t->cfg.ranks[n] : 1;
+  }
+  v.D[0] = 1;
+  v.B = t->cfg.leaf_slices;
+  v.theta_num = t->cfg.theta_num;
+  v.theta_den = t->cfg.theta_den;
+  v.max_iter = t->cfg.max_iter;
+  v.tol = t->cfg.tol;
+  v.T = t->T;
+  v.nb = t->nb;
+  v.nbt = nbt_of(t);
+  v.height = v.nbt > 0 ? ceil_log2(v.nbt) + 1 : 0;
+  v.nlevels = t->nlevels;
+  for (int j = 0; j < TK_MAXL; ++j) v.level_base[j] = t->level_base[j];
+  v.T_cap = t->nbcap * t->cfg.leaf_slices;
+  v.core_pool = t->core_pool.ptr;
+  v.core_stride = t->core_stride;
+  for (int n = 0; n < TK_MAXP; ++n) {
+    v.fac_pool[n] = t->fac_pool[n].ptr;
+    v.fac_stride[n] = t->fac_stride[n];
+  }
+  v.tfac = t->tfac.ptr;
+  v.tfac_level_stride = v.T_cap * t->cfg.ranks[0];
+  v.node_ranks = (int*)t->node_ranks.ptr;
+  return v;
+}
+
+// Arena layout for nbcap leaf blocks: level j holds nbcap >> j slots.
+struct ArenaLayout {
+  int nlevels;
+  int64_t base[TK_MAXL];
+  int64_t nslots;
+};
+
+ArenaLayout layout_for(int64_t nbcap) {
+  ArenaLayout a{};
+  a.nlevels = ceil_log2(nbcap) + 1;
+  int64_t acc = 0;
+  for (int j = 0; j < TK_MAXL; ++j) {
+    a.base[j] = acc;
+    if (j < a.nlevels) acc += std::max<int64_t>(1, nbcap >> j);
+  }
+  a.nslots = acc;
+  return a;
+}
+
+// Grow the arena so that `need_blocks` leaf blocks fit; existing nodes are
+// copied level by level into the new layout.
+int ensure_capacity(tk_tree* t, int64_t need_blocks) {
+  if (need_blocks <= t->nbcap) return TK_OK;
+  const int64_t ncap = next_pow2(std::max<int64_t>(need_blocks, 1));
+  const ArenaLayout L = layout_for(ncap);
+  if (L.nlevels > TK_MAXL) return TK_ERR_TOO_BIG;
+  const int p = t->p;
+  const size_t es = t->es;
+  const int r0 = t->cfg.ranks[0];
+  const int64_t Tcap_new = ncap * t->cfg.leaf_slices;
+  DevBuf core, fac[TK_MAXP], tf, nr;
+  int rc = dalloc(core, (size_t)L.nslots * t->core_stride * es);
+  for (int n = 1; n < p && rc == TK_OK; ++n) rc = dalloc(fac[n], (size_t)L.nslots * t->fac_stride[n] * es);
+  if (rc == TK_OK) rc = dalloc(tf, (size_t)L.nlevels * Tcap_new * r0 * es);
+  if (rc == TK_OK) rc = dalloc(nr, (size_t)L.nslots * TK_MAXP * sizeof(int));
+  if (rc != TK_OK) {
+    dfree(core);
+    for (int n = 0; n < TK_MAXP; ++n) dfree(fac[n]);
+    dfree(tf);
+    dfree(nr);
+    return rc;
+  }
+  cudaMemsetAsync(core.ptr, 0, core.bytes, t->stream);
+  cudaMemsetAsync(tf.ptr, 0, tf.bytes, t->stream);
+  cudaMemsetAsync(nr.ptr, 0, nr.bytes, t->stream);
+  for (int n = 1; n < p; ++n) cudaMemsetAsync(fac[n].ptr, 0, fac[n].bytes, t->stream);
+  if (t->nbcap > 0) {
+    const int64_t Tcap_old = t->nbcap * t->cfg.leaf_slices;
+    for (int j = 0; j < t->nlevels; ++j) {
+      const int64_t cnt = std::max<int64_t>(1, t->nbcap >> j);
+      cudaMemcpyAsync((char*)core.ptr + L.base[j] * t->core_stride * es,
+                      (char*)t->core_pool.ptr + t->level_base[j] * t->core_stride * es,
+                      cnt * t->core_stride * es, cudaMemcpyDeviceToDevice, t->stream);
+      for (int n = 1; n < p; ++n)
+        cudaMemcpyAsync((char*)fac[n].ptr + L.base[j] * t->fac_stride[n] * es,
+                        (char*)t->fac_pool[n].ptr + t->level_base[j] * t->fac_stride[n] * es,
+                        cnt * t->fac_stride[n] * es, cudaMemcpyDeviceToDevice, t->stream);
+      cudaMemcpyAsync((char*)nr.ptr + L.base[j] * TK_MAXP * sizeof(int),
+                      (char*)t->node_ranks.ptr + t->level_base[j] * TK_MAXP * sizeof(int),
+                      cnt * TK_MAXP * sizeof(int), cudaMemcpyDeviceToDevice, t->stream);
+      cudaMemcpyAsync((char*)tf.ptr + (size_t)j * Tcap_new * r0 * es,
+                      (char*)t->tfac.ptr + (size_t)j * Tcap_old * r0 * es, Tcap_old * r0 * es,
+                      cudaMemcpyDeviceToDevice, t->stream);
+    }
+    // the old buffers are released only after the copies ran
+    cudaStreamSynchronize(t->stream);
+  }
+  dfree(t->core_pool);
+  for (int n = 0; n < TK_MAXP; ++n) dfree(t->fac_pool[n]);
+  dfree(t->tfac);
+  dfree(t->node_ranks);
+  t->core_pool = core;
+  for (int n = 0; n < TK_MAXP; ++n) t->fac_pool[n] = fac[n];
+  t->tfac = tf;
+  t->node_ranks = nr;
+  t->nbcap = ncap;
+  t->nlevels = L.nlevels;
+  for (int j = 0; j < TK_MAXL; ++j) t->level_base[j] = L.base[j];
+  t->nslots = L.nslots;
+  // workspaces depend on T_cap and the height: recompute lazily
+  t->ws_stitch_per_cta = 0;
+  t->ws_leaf_per_cta = 0;
+  return TK_OK;
+}
+
+int64_t round32(int64_t x) { return (x + 31) & ~(int64_t)31; }
+
+// Upper bound of a stitch job's workspace (elements), mirroring the device
+// bump allocation of stitch_job with every rank at its build value.
+int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
+  const int p = t->p;
+  const int* r = t->cfg.ranks;
+  int64_t rprod = 1;
+  for (int n = 0; n < p; ++n) rprod *= r[n];
+  const int64_t Tcap = t->nbcap * t->cfg.leaf_slices;
+  int64_t tot = 0;
+  tot += hmax * round32(rprod);
+  tot += 2 * (round32(Tcap * r[0]) + round32(r[0]));  // at most two partial hits
+  int64_t k[TK_MAXP], c[TK_MAXP];
+  int64_t neig = (int64_t)hmax * r[0];
+  k[0] = c[0] = (int64_t)hmax * r[0];
+  for (int n = 1; n < p; ++n) {
+    const int64_t Dn = t->cfg.dims[n];
+    k[n] = (int64_t)hmax * r[n];
+    c[n] = std::min<int64_t>(Dn, k[n]);
+    tot += round32(Dn * k[n]) + round32(k[n]) + round32(c[n] * k[n]) + round32(c[n] * r[n]);
+    neig = std::max(neig, c[n]);
+  }
+  tot += round32(c[0] * r[0]);
+  int64_t Kel = k[0];
+  for (int m = 1; m < p; ++m) Kel *= r[m];
+  tot += round32(Kel);
+  int64_t tb = 0;
+  for (int n = 0; n < p; ++n) {
+    int64_t s = 1;
+    for (int m = 0; m < p; ++m) s *= (m == n) ? std::max<int64_t>(c[m], r[m]) : r[m];
+    tb = std::max(tb, s);
+  }
+  tot += 3 * round32(tb);
+  int64_t wmax = (int64_t)r[0] * r[0];
+  for (int m = 0; m < p; ++m) wmax = std::max<int64_t>(wmax, (int64_t)r[m] * r[m]);
+  tot += round32(wmax);
+  tot += round32(rprod);
+  // eig scratch if it spills out of shared memory
+  tot += 2 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
+  return tot + 256;
+}
+
+int64_t leaf_ws_bound(const tk_tree* t) {
+  const int p = t->p;
+  const int B = t->cfg.leaf_slices;
+  int64_t tot = 0, xel = B, neig = B, gel = 1;
+  tot += round32((int64_t)B * t->cfg.ranks[0]);
+  for (int n = 1; n < p; ++n) {
+    tot += round32(t->cfg.dims[n] * t->cfg.ranks[n]);
+    xel *= t->cfg.dims[n];
+    neig = std::max<int64_t>(neig, t->cfg.dims[n]);
+  }
+  for (int n = 0; n < p; ++n) gel *= t->cfg.ranks[n];
+  tot += 2 * round32(xel) + round32(gel);
+  tot += 2 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
+  return tot + 256;
+}
+
+int max_hits(const tk_tree* t, int64_t nbt) {
+  const int h = nbt > 0 ? ceil_log2(nbt) + 1 : 1;
+  return std::min(TK_MAXH, std::max(2 * (h - 1), 1) + 2);
+}
+
+// Largest eig order kept in shared memory for each kernel family.
+int pick_nsm_stitch(const tk_tree* t) {
+  const int hmax = max_hits(t, std::max<int64_t>(nbt_of(t), t->nbcap));
+  int need = hmax * t->cfg.ranks[0];
+  for (int n = 1; n < t->p; ++n) need = std::max<int>(need, (int)std::min<int64_t>(t->cfg.dims[n], (int64_t)hmax * t->cfg.ranks[n]));
+  const int cap = t->es == 8 ? 64 : 96;
+  return std::max(2, std::min(need, cap));
+}
+
+int pick_nsm_leaf(const tk_tree* t) {
+  int need = t->cfg.leaf_slices;
+  for (int n = 1; n < t->p; ++n) need = std::max<int>(need, (int)t->cfg.dims[n]);
+  const int cap = t->es == 8 ? 110 : 150;
+  return std::max(2, std::min(need, cap));
+}
+
+int ensure_ws_stitch(tk_tree* t, int want_ctas) {
+  const int hmax = max_hits(t, t->nbcap);
+  const int64_t per = stitch_ws_bound(t, hmax);
+  if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
+  int ctas = std::max(1, want_ctas);
+  if (per != t->ws_stitch_per_cta || ctas > t->ws_stitch_ctas) {
+    ctas = std::max(ctas, t->ws_stitch_ctas);
+    const int rc = dalloc(t->ws_stitch, (size_t)per * ctas * t->es);
+    if (rc) return rc;
+    t->ws_stitch_per_cta = per;
+    t->ws_stitch_ctas = ctas;
+  }
+  return TK_OK;
+}
+
+int ensure_ws_leaf(tk_tree* t, int want_ctas) {
+  const int64_t per = leaf_ws_bound(t);
+  if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
+  int ctas = std::max(1, want_ctas);
+  if (per != t->ws_leaf_per_cta || ctas > t->ws_leaf_ctas) {
+    ctas = std::max(ctas, t->ws_leaf_ctas);
+    const int rc = dalloc(t->ws_leaf, (size_t)per * ctas * t->es);
+    if (rc) return rc;
+    t->ws_leaf_per_cta = per;
+    t->ws_leaf_ctas = ctas;
+  }
+  return TK_OK;
+}
+
+TkWorkspace ws_view(const tk_tree* t, bool leaf) {
+  TkWorkspace w{};
+  w.base = leaf ? t->ws_leaf.ptr : t->ws_stitch.ptr;
+  w.per_cta = leaf ? t->ws_leaf_per_cta : t->ws_stitch_per_cta;
+  w.nsm = leaf ? t->nsm_leaf : t->nsm_stitch;
+  w.status = (int*)t->status.ptr;
+  return w;
+}
+
+int grid_for(tk_tree* t, bool leaf, int njobs) {
+  const int dtype = t->cfg.dtype;
+  const size_t smem = leaf ? tk_leaf_smem_bytes(dtype, t->nsm_leaf) : tk_stitch_smem_bytes(dtype, t->nsm_stitch);
+  int occ = tk_occupancy(dtype, leaf ? 0 : 1, smem);
+  if (occ < 1) occ = 1;
+  return std::max(1, std::min(njobs, occ * t->sm_count));
+}
+
+// Decompose leaf blocks [first, first+njobs) read from raw (block stride in
+// elements), each of `ell` slices.
+int run_leaves(tk_tree* t, const void* raw, int64_t block_stride, int64_t first, int njobs, int ell) {
+  if (njobs <= 0) return TK_OK;
+  if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
+  const int grid = grid_for(t, true, njobs);
+  int rc = ensure_ws_leaf(t, grid);
+  if (rc) return rc;
+  rc = tk_launch_leaf(t->cfg.dtype, make_view(t), raw, block_stride, first, njobs, ell, ws_view(t, true), grid,
+                      t->stream);
+  t->launches += 1;
+  return rc;
+}
+
+int run_merges(tk_tree* t, int level, int64_t k0, int njobs) {
+  if (njobs <= 0) return TK_OK;
+  if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
+  const int grid = grid_for(t, false, njobs);
+  int rc = ensure_ws_stitch(t, grid);
+  if (rc) return rc;
+  rc = tk_launch_merge(t->cfg.dtype, make_view(t), level, k0, njobs, ws_view(t, false), grid, t->stream);
+  t->launches += 1;
+  return rc;
+}
+
+// Decompose the open block if slices arrived since its last decomposition.
+int ensure_tail(tk_tree* t) {
+  if (!t->tail_dirty) return TK_OK;
+  const int64_t ell = t->T - t->nb * t->cfg.leaf_slices;
+  int rc = TK_OK;
+  if (ell > 0) rc = run_leaves(t, t->tail_raw.ptr, 0, t->nb, 1, (int)ell);
+  if (rc == TK_OK) t->tail_dirty = false;
+  return rc;
+}
+
+int check_ranks(const tk_tree* t, const int32_t* ranks, int* rq) {
+  for (int n = 0; n < TK_MAXP; ++n) rq[n] = 1;
+  for (int n = 0; n < t->p; ++n) {
+    const int v = ranks ? ranks[n] : t->cfg.ranks[n];
+    if (v < 1 || v > t->cfg.ranks[n]) return TK_ERR_RANK;
+    rq[n] = v;
+  }
+  return TK_OK;
+}
+
+int64_t out_elems(const tk_tree* t, int64_t L, const int* rq) {
+  int64_t c = 1;
+  for (int n = 0; n < t->p; ++n) c *= rq[n];
+  c += L * rq[0];
+  for (int n = 1; n < t->p; ++n) c += t->cfg.dims[n] * rq[n];
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tk_strerror(int code) {
+  switch (code) {
+    case TK_OK: return "ok";
+    case TK_ERR_ARG: return "invalid argument";
+    case TK_ERR_RANGE: return "time range outside [0, T) or empty";
+    case TK_ERR_RANK: return "query rank below 1 or above the build rank";
+    case TK_ERR_NOMEM: return "device allocation failed";
+    case TK_ERR_CUDA: return "CUDA runtime error";
+    case TK_ERR_STATE: return "call not valid in the current tree state";
+    case TK_ERR_WORKSPACE: return "device job exceeded its workspace or hit limit";
+    case TK_ERR_TOO_BIG: return "request exceeds a fixed engine limit";
+    default: return "unknown error";
+  }
+}
+
+int tk_config_default(tk_config* cfg) {
+  if (!cfg) return TK_ERR_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->p = 3;
+  for (int n = 0; n < TK_MAX_MODES; ++n) cfg->ranks[n] = 10;
+  cfg->leaf_slices = 1;
+  cfg->theta_num = 7;
+  cfg->theta_den = 10;
+  cfg->max_iter = 20;
+  cfg->tol = 0.01;
+  cfg->dtype = TK_F32;
+  cfg->device = 0;
+  return TK_OK;
+}
+
+int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out) {
+  if (!cfg || !out) return TK_ERR_ARG;
+  *out = nullptr;
+  if (cfg->p < 2 || cfg->p > TK_MAX_MODES) return TK_ERR_ARG;
+  if (cfg->leaf_slices < 1 || cfg->theta_den < 1 || cfg->theta_num < 1 || cfg->theta_num > cfg->theta_den)
+    return TK_ERR_ARG;
+  if (cfg->max_iter < 1 || (cfg->dtype != TK_F64 && cfg->dtype != TK_F32)) return TK_ERR_ARG;
+  for (int n = 0; n < cfg->p; ++n)
+    if (cfg->ranks[n] < 1 || cfg->ranks[n] > 4096) return TK_ERR_ARG;
+  for (int n = 1; n < cfg->p; ++n)
+    if (cfg->dims[n] < 1 || cfg->dims[n] > (1 << 20)) return TK_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return TK_ERR_CUDA;
+  }
+  tk_tree* t = new (std::nothrow) tk_tree();
+  if (!t) return TK_ERR_NOMEM;
+  t->cfg = *cfg;
+  t->dev = cfg->device;
+  t->p = cfg->p;
+  t->es = cfg->dtype == TK_F64 ? 8 : 4;
+  DeviceGuard g(t->dev);
+  cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->dev);
+  if (cuda_stream) {
+    t->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete t;
+      return TK_ERR_CUDA;
+    }
+    t->own_stream = true;
+  }
+  t->slice_elems = 1;
+  for (int n = 1; n < t->p; ++n) t->slice_elems *= cfg->dims[n];
+  t->core_stride = 1;
+  for (int n = 0; n < t->p; ++n) t->core_stride *= cfg->ranks[n];
+  for (int n = 1; n < t->p; ++n) t->fac_stride[n] = cfg->dims[n] * cfg->ranks[n];
+  int rc = dalloc(t->tail_raw, (size_t)cfg->leaf_slices * t->slice_elems * t->es);
+  if (rc == TK_OK) rc = dalloc(t->status, 64);
+  if (rc == TK_OK) rc = cuda_ok(cudaMemsetAsync(t->status.ptr, 0, 64, t->stream));
+  if (rc == TK_OK) rc = ensure_capacity(t, 1);
+  if (rc != TK_OK) {
+    tk_tree_destroy(t);
+    return rc;
+  }
+  *out = t;
+  return TK_OK;
+}
+
+void tk_tree_destroy(tk_tree* t) {
+  if (!t) return;
+  DeviceGuard g(t->dev);
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  DevBuf* bufs[] = {&t->core_pool, &t->tfac, &t->node_ranks, &t->tail_raw, &t->ws_stitch, &t->ws_leaf,
+                    &t->status, &t->stage_in, &t->stage_out, &t->stage_meta, &t->stage_info, &t->hit_buf};
+  for (DevBuf* b : bufs) dfree(*b);
+  for (int n = 0; n < TK_MAXP; ++n) dfree(t->fac_pool[n]);
+  if (t->own_stream && t->stream) cudaStreamDestroy(t->stream);
+  delete t;
+}
+
+int64_t tk_timespan(const tk_tree* t) { return t ? t->T : -1; }
+int64_t tk_launch_count(const tk_tree* t) { return t ? t->launches : -1; }
+
+int64_t tk_arena_bytes(const tk_tree* t) {
+  if (!t) return -1;
+  int64_t b = t->core_pool.bytes + t->tfac.bytes + t->node_ranks.bytes;
+  for (int n = 0; n < TK_MAXP; ++n) b += t->fac_pool[n].bytes;
+  return b;
+}
+
+int tk_sync(tk_tree* t) {
+  if (!t) return TK_ERR_ARG;
+  DeviceGuard g(t->dev);
+  if (cudaStreamSynchronize(t->stream) != cudaSuccess) return TK_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, t->status.ptr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TK_ERR_CUDA;
+  if (st == TK_DEV_ERR_RANGE) return TK_ERR_RANGE;
+  if (st != 0) return TK_ERR_WORKSPACE;
+  return TK_OK;
+}
+
+int tk_tree_build(tk_tree* t, const void* X, int64_t T, int io) {
+  if (!t || !X || T < 1) return TK_ERR_ARG;
+  if (t->T != 0) return TK_ERR_STATE;
+  DeviceGuard g(t->dev);
+  const int B = t->cfg.leaf_slices;
+  const int64_t nb = T / B, nbt = (T + B - 1) / B;
+  int rc = ensure_capacity(t, nbt);
+  if (rc) return rc;
+  const void* Xd = X;
+  DevBuf tmp;
+  if (io == TK_IO_HOST) {
+    rc = dalloc(tmp, (size_t)T * t->slice_elems * t->es);
+    if (rc) return rc;
+    rc = cuda_ok(cudaMemcpyAsync(tmp.ptr, X, tmp.bytes, cudaMemcpyHostToDevice, t->stream));
+    if (rc) {
+      dfree(tmp);
+      return rc;
+    }
+    Xd = tmp.ptr;
+  }
+  // complete leaf blocks, then each level of intermediate nodes
+  t->T = nb * B;
+  t->nb = nb;
+  rc = run_leaves(t, Xd, (int64_t)B * t->slice_elems, 0, (int)nb, B);
+  for (int j = 1; rc == TK_OK; ++j) {
+    const int64_t cnt = nb >> j;
+    if (cnt <= 0) break;
+    rc = run_merges(t, j, 0, (int)cnt);
+  }
+  // open tail block
+  if (rc == TK_OK && T > nb * B) {
+    const int64_t ell = T - nb * B;
+    rc = cuda_ok(cudaMemcpyAsync(t->tail_raw.ptr, (const char*)Xd + (size_t)nb * B * t->slice_elems * t->es,
+                                 (size_t)ell * t->slice_elems * t->es, cudaMemcpyDeviceToDevice, t->stream));
+    t->T = T;
+    t->tail_dirty = true;
+  }
+  if (tmp.ptr) {
+    cudaStreamSynchronize(t->stream);
+    dfree(tmp);
+  }
+  return rc;
+}
+
+int tk_stream_append(tk_tree* t, const void* slice, int io) {
+  if (!t || !slice) return TK_ERR_ARG;
+  DeviceGuard g(t->dev);
+  const int B = t->cfg.leaf_slices;
+  int rc = ensure_capacity(t, (t->T + 1 + B - 1) / B);
+  if (rc) return rc;
+  const int64_t off = t->T - t->nb * B;
+  char* dst = (char*)t->tail_raw.ptr + (size_t)off * t->slice_elems * t->es;
+  rc = cuda_ok(cudaMemcpyAsync(dst, slice, (size_t)t->slice_elems * t->es,
+                               io == TK_IO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, t->stream));
+  if (rc) return rc;
+  if (io == TK_IO_HOST) cudaStreamSynchronize(t->stream);  // the caller may reuse its host buffer
+  t->T += 1;
+  if (off + 1 == B) {
+    // Algorithm 3: the leaf completes, then every ancestor whose range ends here is stitched
+    t->tail_dirty = false;
+    rc = run_leaves(t, t->tail_raw.ptr, 0, t->nb, 1, B);
+    t->nb += 1;
+    for (int j = 1; rc == TK_OK; ++j) {
+      if (t->nb % ((int64_t)1 << j) != 0) break;
+      rc = run_merges(t, j, (t->nb >> j) - 1, 1);
+    }
+  } else {
+    t->tail_dirty = true;
+  }
+  return rc;
+}
+
+int tk_hit_set(tk_tree* t, int64_t t_s, int64_t t_e, tk_hit* out, int cap, int* n_out) {
+  if (!t || !out || !n_out || cap < 1) return TK_ERR_ARG;
+  if (!(t_s >= 0 && t_s < t_e && t_e <= t->T)) return TK_ERR_RANGE;
+  DeviceGuard g(t->dev);
+  const size_t need = 64 + sizeof(int64_t) * 2 + sizeof(tk_hit) * TK_MAXH;
+  int rc = dalloc(t->hit_buf, need);
+  if (rc) return rc;
+  int64_t rng[2] = {t_s, t_e};
+  char* base = (char*)t->hit_buf.ptr;
+  int* counts = (int*)base;
+  int64_t* dr = (int64_t*)(base + 16);
+  tk_hit* dh = (tk_hit*)(base + 64);
+  rc = cuda_ok(cudaMemcpyAsync(dr, rng, sizeof(rng), cudaMemcpyHostToDevice, t->stream));
+  if (rc) return rc;
+  rc = tk_launch_hitset(make_view(t), 1, dr, dh, TK_MAXH, counts, t->stream);
+  t->launches += 1;
+  if (rc) return rc;
+  int cnt = 0;
+  std::vector<tk_hit> h(TK_MAXH);
+  rc = cuda_ok(cudaMemcpyAsync(&cnt, counts, sizeof(int), cudaMemcpyDeviceToHost, t->stream));
+  if (rc == TK_OK) rc = cuda_ok(cudaMemcpyAsync(h.data(), dh, sizeof(tk_hit) * TK_MAXH, cudaMemcpyDeviceToHost, t->stream));
+  if (rc == TK_OK) rc = cuda_ok(cudaStreamSynchronize(t->stream));
+  if (rc) return rc;
+  if (cnt < 0) return TK_ERR_TOO_BIG;
+  *n_out = cnt;
+  if (cnt > cap) return TK_ERR_TOO_BIG;
+  std::memcpy(out, h.data(), sizeof(tk_hit) * cnt);
+  return TK_OK;
+}
+
+int64_t tk_query_output_elems(const tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks) {
+  if (!t) return TK_ERR_ARG;
+  if (!(t_s >= 0 && t_s < t_e)) return TK_ERR_RANGE;
+  int rq[TK_MAXP];
+  const int rc = check_ranks(t, ranks, rq);
+  if (rc) return rc;
+  return out_elems(t, t_e - t_s, rq);
+}
+
+int tk_batch_layout(const tk_tree* t, int n, const int64_t* ranges, const int32_t* ranks, int64_t* offsets) {
+  if (!t || n < 0 || (n > 0 && (!ranges || !offsets))) return TK_ERR_ARG;
+  int rq[TK_MAXP];
+  const int rc = check_ranks(t, ranks, rq);
+  if (rc) return rc;
+  offsets[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t ts = ranges[2 * i], te = ranges[2 * i + 1];
+    if (!(ts >= 0 && ts < te)) return TK_ERR_RANGE;
+    offsets[i + 1] = offsets[i] + out_elems(t, te - ts, rq);
+  }
+  return TK_OK;
+}
+
+int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t* offsets, const int32_t* ranks,
+                         void* out, tk_query_info* info, int io) {
+  if (!t || n < 0) return TK_ERR_ARG;
+  if (n == 0) return TK_OK;
+  if (!ranges || !offsets || !out) return TK_ERR_ARG;
+  DeviceGuard g(t->dev);
+  int rq[TK_MAXP];
+  int rc = check_ranks(t, ranks, rq);
+  if (rc) return rc;
+  if (t->T == 0) return TK_ERR_RANGE;
+  if (io == TK_IO_HOST) {
+    for (int i = 0; i < n; ++i)
+      if (!(ranges[2 * i] >= 0 && ranges[2 * i] < ranges[2 * i + 1] && ranges[2 * i + 1] <= t->T)) return TK_ERR_RANGE;
+  }
+  rc = ensure_tail(t);
+  if (rc) return rc;
+  const int64_t* d_ranges = ranges;
+  const int64_t* d_offsets = offsets;
+  void* d_out = out;
+  if (io == TK_IO_HOST) {
+    const size_t meta = sizeof(int64_t) * (2 * (size_t)n + n + 1);
+    rc = dalloc(t->stage_meta, meta);
+    if (rc) return rc;
+    rc = dalloc(t->stage_out, (size_t)offsets[n] * t->es);
+    if (rc) return rc;
+    int64_t* m = (int64_t*)t->stage_meta.ptr;
+    rc = cuda_ok(cudaMemcpyAsync(m, ranges, sizeof(int64_t) * 2 * n, cudaMemcpyHostToDevice, t->stream));
+    if (rc == TK_OK)
+      rc = cuda_ok(cudaMemcpyAsync(m + 2 * n, offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, t->stream));
+    if (rc) return rc;
+    d_ranges = m;
+    d_offsets = m + 2 * n;
+    d_out = t->stage_out.ptr;
+  }
+  tk_query_info* d_info = nullptr;
+  if (info) {
+    rc = dalloc(t->stage_info, sizeof(tk_query_info) * n);
+    if (rc) return rc;
+    d_info = (tk_query_info*)t->stage_info.ptr;
+  }
+  if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
+  const int grid = grid_for(t, false, n);
+  rc = ensure_ws_stitch(t, grid);
+  if (rc) return rc;
+  TkQueryBatch qb{};
+  qb.n = n;
+  qb.ranges = d_ranges;
+  qb.offsets = d_offsets;
+  qb.out = d_out;
+  qb.info = d_info;
+  for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
+  rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
+  t->launches += 1;
+  if (rc) return rc;
+  if (io == TK_IO_HOST) {
+    rc = cuda_ok(cudaMemcpyAsync(out, d_out, (size_t)offsets[n] * t->es, cudaMemcpyDeviceToHost, t->stream));
+    if (rc) return rc;
+  }
+  if (info) {
+    rc = cuda_ok(cudaMemcpyAsync(info, d_info, sizeof(tk_query_info) * n, cudaMemcpyDeviceToHost, t->stream));
+    if (rc) return rc;
+  }
+  if (io == TK_IO_HOST || info) {
+    rc = tk_sync(t);
+    if (rc) return rc;
+  }
+  return TK_OK;
+}
+
+int tk_range_query(tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks, void* out, tk_query_info* info,
+                   int io) {
+  if (!t || !out) return TK_ERR_ARG;
+  if (!(t_s >= 0 && t_s < t_e && t_e <= t->T)) return TK_ERR_RANGE;
+  int rq[TK_MAXP];
+  int rc = check_ranks(t, ranks, rq);
+  if (rc) return rc;
+  int64_t rng[2] = {t_s, t_e};
+  int64_t offs[2] = {0, out_elems(t, t_e - t_s, rq)};
+  DeviceGuard g(t->dev);
+  if (io == TK_IO_HOST) return tk_range_query_batch(t, 1, rng, offs, ranks, out, info, TK_IO_HOST);
+  // device output: the two small arrays go through the metadata staging buffer
+  rc = dalloc(t->stage_meta, std::max<size_t>(t->stage_meta.bytes, sizeof(int64_t) * 4));
+  if (rc) return rc;
+  int64_t* m = (int64_t*)t->stage_meta.ptr;
+  int64_t hm[4] = {t_s, t_e, 0, offs[1]};
+  rc = cuda_ok(cudaMemcpyAsync(m, hm, sizeof(hm), cudaMemcpyHostToDevice, t->stream));
+  if (rc) return rc;
+  // the host array must outlive the async copy
+  rc = cuda_ok(cudaStreamSynchronize(t->stream));
+  if (rc) return rc;
+  return tk_range_query_batch(t, 1, m, m + 2, ranks, out, info, TK_IO_DEVICE);
+}
+
+int tk_node_payload(tk_tree* t, int level, int64_t index, void* out_host, int64_t out_elems_cap, int32_t* ranks_out) {
+  if (!t || !out_host || level < 0 || index < 0) return TK_ERR_ARG;
+  DeviceGuard g(t->dev);
+  int rc = ensure_tail(t);
+  if (rc) return rc;
+  const int B = t->cfg.leaf_slices;
+  const int64_t nbt = nbt_of(t);
+  const bool complete = ((index + 1) << level) <= t->nb;
+  const bool tail = level == 0 && index == t->nb && t->T > t->nb * B;
+  if (!complete && !tail) return TK_ERR_RANGE;
+  (void)nbt;
+  const int64_t lo = (index << level) * B;
+  const int64_t hi = std::min<int64_t>(lo + ((int64_t)1 << level) * B, t->T);
+  const int* r = t->cfg.ranks;
+  int rq[TK_MAXP];
+  for (int n = 0; n < TK_MAXP; ++n) rq[n] = n < t->p ? r[n] : 1;
+  const int64_t need = out_elems(t, hi - lo, rq);
+  if (out_elems_cap < need) return TK_ERR_ARG;
+  const int64_t slot = t->level_base[level] + index;
+  char* o = (char*)out_host;
+  const size_t es = t->es;
+  rc = cuda_ok(cudaMemcpyAsync(o, (char*)t->core_pool.ptr + slot * t->core_stride * es, t->core_stride * es,
+                               cudaMemcpyDeviceToHost, t->stream));
+  o += t->core_stride * es;
+  const int64_t Tcap = t->nbcap * B;
+  if (rc == TK_OK)
+    rc = cuda_ok(cudaMemcpyAsync(o, (char*)t->tfac.ptr + ((size_t)level * Tcap + lo) * r[0] * es,
+                                 (size_t)(hi - lo) * r[0] * es, cudaMemcpyDeviceToHost, t->stream));
+  o += (size_t)(hi - lo) * r[0] * es;
+  for (int n = 1; n < t->p && rc == TK_OK; ++n) {
+    rc = cuda_ok(cudaMemcpyAsync(o, (char*)t->fac_pool[n].ptr + slot * t->fac_stride[n] * es,
+                                 t->fac_stride[n] * es, cudaMemcpyDeviceToHost, t->stream));
+    o += t->fac_stride[n] * es;
+  }
+  int nr[TK_MAXP];
+  if (rc == TK_OK)
+    rc = cuda_ok(cudaMemcpyAsync(nr, (char*)t->node_ranks.ptr + slot * TK_MAXP * sizeof(int), sizeof(nr),
+                                 cudaMemcpyDeviceToHost, t->stream));
+  if (rc == TK_OK) rc = tk_sync(t);
+  if (rc == TK_OK && ranks_out)
+    for (int n = 0; n < TK_MAXP; ++n) ranks_out[n] = nr[n];
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal declarations shared by the engine (host) and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tucket.h"
+
+#define TK_MAXP TK_MAX_MODES
+#define TK_MAXL 40      // tree levels (2^39 leaf blocks)
+#define TK_MAXH 64      // hits per stitch job handled by the kernel
+#define TK_NT 256       // threads per CTA of the stitch and leaf kernels
+
+// Device view of a tree: dimensions, the implicit dyadic node numbering and
+// the pooled HBM arena.  Passed by value to every kernel.
+//
+// Node (level j, index k) covers leaf blocks [k 2^j, (k+1) 2^j), i.e. slices
+// [k 2^j B, min((k+1) 2^j B, T)).  It is complete (a leaf or an intermediate
+// node of Section 4.2) iff (k+1) 2^j <= nb, the number of complete blocks; the
+// open block (level 0, index nb, when T > nb B) is the tail leaf.  Its slot
+// is level_base[j] + k.
+struct TkTreeView {
+  int p;
+  int D[TK_MAXP];          // D[0] unused (time)
+  int r[TK_MAXP];          // build ranks (slot capacities)
+  int B;
+  int theta_num, theta_den;
+  int max_iter;
+  double tol;
+  int64_t T, nb, nbt;      // slices, complete blocks, blocks incl. the tail
+  int height;              // ceil(log2 nbt) + 1, 0 when empty
+  int nlevels;
+  int64_t level_base[TK_MAXL];
+  int64_t T_cap;           // rows per level of the temporal arrays
+  void* core_pool;         // slot * core_stride, capacity dims r[0..p-1]
+  int64_t core_stride;
+  void* fac_pool[TK_MAXP]; // mode n >= 1: slot * fac_stride[n], D_n x r_n rows
+  int64_t fac_stride[TK_MAXP];
+  void* tfac;              // level * tfac_level_stride + t * r[0]: temporal rows
+  int64_t tfac_level_stride;
+  int* node_ranks;         // slot * TK_MAXP: logical ranks of the stored node
+};
+
+struct TkWorkspace {
+  void* base;              // per-CTA chunks of `per_cta` elements
+  int64_t per_cta;
+  int nsm;                 // largest eig order kept in shared memory
+  int* status;             // first device-side error (0 = none)
+};
+
+enum { TK_JOB_QUERY = 0, TK_JOB_MERGE = 1 };
+
+struct TkQueryBatch {
+  int n;
+  const int64_t* ranges;   // device, 2n
+  const int64_t* offsets;  // device, n+1
+  void* out;               // device
+  tk_query_info* info;     // device, n (may be null)
+  int rq[TK_MAXP];         // requested ranks
+};
+
+// Launchers (tk_kernels.cu).  All asynchronous on `stream`.
+int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t block_stride,
+                   int64_t first_block, int njobs, int ell, const TkWorkspace& ws, int grid,
+                   cudaStream_t stream);
+int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int njobs,
+                    const TkWorkspace& ws, int grid, cudaStream_t stream);
+int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb,
+                    const TkWorkspace& ws, int grid, cudaStream_t stream);
+int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap,
+                     int* counts, cudaStream_t stream);
+
+// Shared-memory bytes of the two kernel families for a given in-smem eig order.
+size_t tk_stitch_smem_bytes(int dtype, int nsm);
+size_t tk_leaf_smem_bytes(int dtype, int nsm);
+int tk_occupancy(int dtype, int which /*0 leaf, 1 stitch*/, size_t smem);
+
+enum { TK_DEV_ERR_WORKSPACE = 1, TK_DEV_ERR_HITS = 2, TK_DEV_ERR_RANGE = 3 };

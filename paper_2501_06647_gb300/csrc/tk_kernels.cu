@@ -1,0 +1,898 @@
+// Kernels of the range-query Tucker engine.
+//
+//  k_hitset  Algorithm 1 (Recall) over the implicit dyadic stream segment tree.
+//  k_stitch  one CTA per job; a job is a range query (Section 6.1: Recall,
+//            Eq. (partial-tucker), Algorithm 2) or the re-decomposition of a
+//            newly complete node from its two children (Algorithm 3, Stitch).
+//  k_leaf    one CTA per leaf block: Tucker-ALS (Section 2) of the raw block.
+//
+// Stitch runs in coefficient space.  Every V~_i^(1) has orthonormal columns
+// and the hits occupy disjoint time rows, so Z^(1) of Eq. (stitch-temp-2)
+// equals blockdiag(V~_i^(1)) K with K = [mat_1(H~_i x_{m>=2} W_im)]_i,
+// W_im = U^(m)T V~_i^(m), and the leading left singular vectors of Z^(1) are
+// blockdiag(V~_i^(1)) times the leading eigenvectors C of K K^T.  Hence
+// U^(1)T_[t_{i-1},t_i) V~_i^(1) = C_i^T (the block rows of C).  For a
+// non-temporal mode n, Phi_n = [V~_1^(n) ... V~_s^(n)] = Q_n R_n (Householder,
+// once per job) turns Z^(n) of Eq. (stitch-nontemp-3) into Q_n N_n with
+// N_n = sum_i mat_n(H~_i x_1 C_i^T x_{m!=1,n} W_im x_n R_n[:,blk i]); then
+// U^(n) = Q_n E_n with E_n the leading eigenvectors of N_n N_n^T and
+// W_im = E_m^T R_m[:,blk i].  The core is N_p x_p E_p^T (Algorithm 2's last
+// step).  The loop never touches D or L: they enter only through the QR of
+// Phi_n and the final factor assembly.  This is an exact rewrite: the result
+// is Algorithm 2's iterate, up to rounding order.
+#include <cstdio>
+
+#include "tk_device.cuh"
+#include "tk_internal.h"
+
+namespace tk {
+
+struct HitRec {
+  int level, partial;
+  int64_t index, node_lo, node_hi, lo, hi, slot;
+  int64_t toff;       // row offset t_{i-1} of the hit in U^(1)
+  int64_t core_off;   // workspace offset of H~_i (dims q)
+  int64_t slice_off;  // workspace offset of the partial slice (reflectors)
+  int64_t stau_off;   // workspace offset of its tau
+  int q[TK_MAXP];     // ranks of H~_i
+  int nr0;            // stored temporal rank of the node
+  int koff[TK_MAXP];  // column offset of the hit's block in mode n's coefficient space
+};
+
+struct StitchCtx {
+  int nh, err, L_int;
+  int64_t L;
+  int ro[TK_MAXP];
+  int k[TK_MAXP];     // sum_i q_i[n]
+  int c[TK_MAXP];     // coefficient dimension: k[0] for time, min(D_n, k_n) otherwise
+  int qmax[TK_MAXP];
+  int64_t off_phi[TK_MAXP], off_tau[TK_MAXP], off_R[TK_MAXP], off_E[TK_MAXP];
+  int64_t off_K, off_b0, off_b1, off_N, off_W, off_G, off_A, off_V, off_w, off_cs, off_pq;
+  int neig;           // largest eig order of the job
+  int eig_in_smem;
+};
+
+__device__ __forceinline__ int64_t node_lo_of(const TkTreeView& tv, int j, int64_t k) {
+  return (k << j) * (int64_t)tv.B;
+}
+
+// Algorithm 1 (Recall) on the implicit tree; writes up to cap hits in time
+// order.  theta test in integers: theta_den * overlap >= theta_num * |v|.
+// Leaves are terminal: an overlapping leaf (complete or tail) is a hit.
+// Returns the hit count, or -1 if more than cap hits were found.
+__device__ int recall_dev(const TkTreeView& tv, int64_t ts, int64_t te, HitRec* hits, int cap) {
+  if (tv.height <= 0) return 0;
+  int sj[2 * TK_MAXL + 4];
+  int64_t sk[2 * TK_MAXL + 4];
+  int sp = 0, nh = 0;
+  sj[0] = tv.height - 1;
+  sk[0] = 0;
+  sp = 1;
+  while (sp > 0) {
+    --sp;
+    const int j = sj[sp];
+    const int64_t k = sk[sp];
+    const int64_t w = ((int64_t)1 << j) * tv.B;
+    const int64_t lo = k * w;
+    int64_t hi = lo + w;
+    if (hi > tv.T) hi = tv.T;
+    const int64_t a = ts > lo ? ts : lo, b = te < hi ? te : hi;
+    const int64_t ov = b > a ? b - a : 0;
+    const bool complete = ((k + 1) << j) <= tv.nb;
+    bool hit = false;
+    if (j == 0) hit = (k < tv.nbt) && ov > 0;
+    else if (complete) hit = (int64_t)tv.theta_den * ov >= (int64_t)tv.theta_num * (hi - lo);
+    if (hit) {
+      if (nh >= cap) return -1;
+      HitRec& h = hits[nh++];
+      h.level = j;
+      h.index = k;
+      h.node_lo = lo;
+      h.node_hi = hi;
+      h.lo = a;
+      h.hi = b;
+      h.partial = (a != lo || b != hi) ? 1 : 0;
+      continue;
+    }
+    if (j == 0) continue;
+    const int64_t mu = (2 * k + 1) * (w / 2);
+    if (te <= mu) {
+      sj[sp] = j - 1; sk[sp] = 2 * k; ++sp;
+    } else if (ts >= mu) {
+      sj[sp] = j - 1; sk[sp] = 2 * k + 1; ++sp;
+    } else {
+      sj[sp] = j - 1; sk[sp] = 2 * k + 1; ++sp;
+      sj[sp] = j - 1; sk[sp] = 2 * k; ++sp;
+    }
+  }
+  return nh;
+}
+
+__device__ void set_err(int* status, int code) { atomicCAS(status, 0, code); }
+
+// Output-rank clamp of a stitch: r_n' = min(r_n, extent_n, sum_i min(q_in,
+// prod_{m!=n} q_im)), then r_n' <= prod_{m!=n} r_m' to a fixpoint.
+__device__ void stitch_ranks(int p, const int* rq, const int64_t* ext, const HitRec* hits, int nh, int* ro) {
+  for (int n = 0; n < p; ++n) {
+    int64_t cap = 0;
+    for (int i = 0; i < nh; ++i) {
+      int64_t prod = 1;
+      for (int m = 0; m < p; ++m)
+        if (m != n) prod *= hits[i].q[m];
+      cap += hits[i].q[n] < prod ? hits[i].q[n] : prod;
+    }
+    int64_t v = rq[n];
+    if (ext[n] < v) v = ext[n];
+    if (cap < v) v = cap;
+    ro[n] = (int)v;
+  }
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int n = 0; n < p; ++n) {
+      int64_t prod = 1;
+      for (int m = 0; m < p; ++m)
+        if (m != n) prod *= ro[m];
+      if (ro[n] > prod) {
+        ro[n] = (int)prod;
+        changed = true;
+      }
+    }
+  }
+}
+
+template <class S> struct Smem {
+  HitRec hits[TK_MAXH];
+  StitchCtx ctx;
+  S red[40];
+  S sc[4];
+  int flag;
+  int pq[1];  // followed by the Jacobi arrays (see layout())
+};
+
+// W (ro_m x q) = E_m^T R_m[:, koff .. koff+q): both row-major in the workspace.
+template <class S>
+__device__ void proj_coef(const S* E, int cm, int rom, const S* R, int km, int koff, int q, S* W) {
+  gemm<S>(rom, q, cm, E, 1, rom, R + koff, km, 1, W, q, 1, false);
+}
+
+// The job body shared by range queries and node merges.
+template <class S>
+__device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t te, int mlevel, int64_t mindex,
+                           const int* rq, S* ws, int64_t ws_cap, int nsm, S* core_dst, S* u0_dst, int64_t ld0,
+                           S* const* un_dst, const int64_t* ldn, int* ranks_dst, tk_query_info* info,
+                           int* status, unsigned char* smem_raw) {
+  Smem<S>& sm = *reinterpret_cast<Smem<S>*>(smem_raw);
+  StitchCtx& cx = sm.ctx;
+  HitRec* hits = sm.hits;
+  const int p = tv.p;
+  const int tid = threadIdx.x;
+  // Jacobi scratch in shared memory (after the fixed part).
+  const int half_cap = nsm / 2 + 2;
+  int* js_pq = sm.pq;
+  S* js_cs = reinterpret_cast<S*>(((uintptr_t)(js_pq + half_cap) + 15) & ~(uintptr_t)15);
+  S* js_w = js_cs + 2 * half_cap;
+  S* sA = js_w + nsm + 2;
+  S* sV = sA + (int64_t)nsm * nsm;
+
+  if (tid == 0) {
+    cx.err = 0;
+    int nh = 0;
+    if (mode == TK_JOB_QUERY) {
+      nh = recall_dev(tv, ts, te, hits, TK_MAXH);
+      if (nh < 0) cx.err = TK_DEV_ERR_HITS;
+    } else {
+      nh = 2;
+      for (int c = 0; c < 2; ++c) {
+        HitRec& h = hits[c];
+        h.level = mlevel - 1;
+        h.index = 2 * mindex + c;
+        h.node_lo = node_lo_of(tv, h.level, h.index);
+        h.node_hi = h.node_lo + ((int64_t)1 << h.level) * tv.B;
+        h.lo = h.node_lo;
+        h.hi = h.node_hi;
+        h.partial = 0;
+      }
+    }
+    if (nh <= 0 && cx.err == 0) cx.err = TK_DEV_ERR_RANGE;
+    cx.nh = nh > 0 ? nh : 0;
+    int64_t L = 0;
+    for (int i = 0; i < cx.nh; ++i) {
+      HitRec& h = hits[i];
+      h.slot = tv.level_base[h.level] + h.index;
+      const int* nr = tv.node_ranks + h.slot * TK_MAXP;
+      const int64_t ell = h.hi - h.lo;
+      h.nr0 = nr[0];
+      h.q[0] = h.partial ? (int)(ell < nr[0] ? ell : nr[0]) : nr[0];
+      for (int n = 1; n < p; ++n) h.q[n] = nr[n];
+      h.toff = L;
+      L += ell;
+    }
+    cx.L = L;
+    int64_t ext[TK_MAXP];
+    ext[0] = L;
+    for (int n = 1; n < p; ++n) ext[n] = tv.D[n];
+    stitch_ranks(p, rq, ext, hits, cx.nh, cx.ro);
+    for (int n = 0; n < p; ++n) {
+      int kk = 0, qm = 0;
+      for (int i = 0; i < cx.nh; ++i) {
+        hits[i].koff[n] = kk;
+        kk += hits[i].q[n];
+        if (hits[i].q[n] > qm) qm = hits[i].q[n];
+      }
+      cx.k[n] = kk;
+      cx.qmax[n] = qm;
+      cx.c[n] = (n == 0) ? kk : (tv.D[n] < kk ? tv.D[n] : kk);
+    }
+    // workspace layout (bump allocation, 32-element aligned)
+    int64_t cur = 0;
+    auto take = [&](int64_t nel) {
+      const int64_t o = cur;
+      cur += (nel + 31) & ~(int64_t)31;
+      return o;
+    };
+    for (int i = 0; i < cx.nh; ++i) {
+      HitRec& h = hits[i];
+      int64_t cs = 1;
+      for (int n = 0; n < p; ++n) cs *= (h.q[n] > (n == 0 ? h.nr0 : h.q[n]) ? h.q[n] : (n == 0 ? h.nr0 : h.q[n]));
+      h.core_off = take(cs);
+      if (h.partial) {
+        h.slice_off = take((h.hi - h.lo) * (int64_t)h.nr0);
+        h.stau_off = take(h.nr0);
+      } else {
+        h.slice_off = h.stau_off = 0;
+      }
+    }
+    int neig = cx.c[0];
+    for (int n = 1; n < p; ++n) {
+      cx.off_phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
+      cx.off_tau[n] = take(cx.k[n]);
+      cx.off_R[n] = take((int64_t)cx.c[n] * cx.k[n]);
+      cx.off_E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
+      if (cx.c[n] > neig) neig = cx.c[n];
+    }
+    cx.off_E[0] = take((int64_t)cx.c[0] * cx.ro[0]);
+    int64_t Kel = cx.k[0];
+    for (int m = 1; m < p; ++m) Kel *= cx.ro[m];
+    cx.off_K = take(Kel);
+    // chain buffers: every intermediate has, per mode, at most max(q_max, ro, nr0) (or c_n) entries
+    int64_t tb = 0;
+    for (int n = 0; n < p; ++n) {
+      int64_t s = 1;
+      for (int m = 0; m < p; ++m) {
+        int e = cx.qmax[m] > cx.ro[m] ? cx.qmax[m] : cx.ro[m];
+        if (m == 0 && tv.r[0] > e) e = tv.r[0];
+        if (m == n && cx.c[m] > e) e = cx.c[m];
+        s *= e;
+      }
+      if (s > tb) tb = s;
+    }
+    cx.off_b0 = take(tb);
+    cx.off_b1 = take(tb);
+    cx.off_N = take(tb);
+    int wmax = tv.r[0] * tv.r[0];
+    for (int m = 0; m < p; ++m) {
+      const int v = cx.ro[m] * (cx.qmax[m] > 1 ? cx.qmax[m] : 1);
+      if (v > wmax) wmax = v;
+    }
+    cx.off_W = take(wmax);
+    int64_t gel = 1;
+    for (int n = 0; n < p; ++n) gel *= cx.ro[n];
+    cx.off_G = take(gel);
+    cx.neig = neig;
+    cx.eig_in_smem = neig <= nsm;
+    if (!cx.eig_in_smem) {
+      cx.off_A = take((int64_t)neig * neig);
+      cx.off_V = take((int64_t)neig * neig);
+      cx.off_w = take(neig + 2);
+      cx.off_cs = take(2 * (neig / 2 + 2));
+      cx.off_pq = take(((neig / 2 + 2) * (int64_t)sizeof(int) + sizeof(S) - 1) / sizeof(S));
+    } else {
+      cx.off_A = cx.off_V = cx.off_w = cx.off_cs = cx.off_pq = 0;
+    }
+    if (cur > ws_cap && cx.err == 0) cx.err = TK_DEV_ERR_WORKSPACE;
+  }
+  __syncthreads();
+  if (cx.err) {
+    if (tid == 0) {
+      set_err(status, cx.err);
+      if (info) {
+        info->iters = -cx.err;
+        info->n_hits = cx.nh;
+      }
+    }
+    return;
+  }
+  const int nh = cx.nh;
+  S* A = cx.eig_in_smem ? sA : ws + cx.off_A;
+  S* V = cx.eig_in_smem ? sV : ws + cx.off_V;
+  S* wv = cx.eig_in_smem ? js_w : ws + cx.off_w;
+  if (!cx.eig_in_smem) {
+    js_cs = ws + cx.off_cs;
+    js_pq = reinterpret_cast<int*>(ws + cx.off_pq);
+  }
+  JacobiScratch js{js_pq, &sm.flag};
+  const int maxsw = sizeof(S) == 8 ? 24 : 16;
+  int dims[TK_MAXP];
+
+  // ---- hit decompositions: stored payloads or Eq. (partial-tucker) -------
+  S hn2 = 0;
+  for (int i = 0; i < nh; ++i) {
+    const HitRec& h = hits[i];
+    const S* core = reinterpret_cast<const S*>(tv.core_pool) + h.slot * tv.core_stride;
+    const int* nr = tv.node_ranks + h.slot * TK_MAXP;
+    S* Hc = ws + h.core_off;
+    if (!h.partial) {
+      int64_t tot = 1;
+      for (int n = 0; n < p; ++n) tot *= h.q[n];
+      for (int64_t idx = tid; idx < tot; idx += blockDim.x) {
+        int64_t rem = idx, src = 0, strd = 1;
+        for (int n = p - 1; n >= 0; --n) {
+          const int in = (int)(rem % h.q[n]);
+          rem /= h.q[n];
+          src += in * strd;
+          strd *= tv.r[n];
+        }
+        Hc[idx] = core[src];
+      }
+      __syncthreads();
+    } else {
+      // slice rows of the node's temporal factor, QR, then H x_1 R~
+      const int64_t ell = h.hi - h.lo;
+      const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride;
+      S* sl = ws + h.slice_off;
+      const int nr0 = h.nr0;
+      for (int64_t idx = tid; idx < ell * nr0; idx += blockDim.x) {
+        const int64_t t = idx / nr0;
+        const int c = (int)(idx % nr0);
+        sl[idx] = tf[(h.lo + t) * tv.r[0] + c];
+      }
+      __syncthreads();
+      householder_qr<S>(sl, (int)ell, nr0, nr0, ws + h.stau_off, sm.sc);
+      // stored core (logical dims nr) into the chain buffer, then x_1 R~
+      int64_t tot = 1;
+      for (int n = 0; n < p; ++n) {
+        dims[n] = nr[n];
+        tot *= nr[n];
+      }
+      S* b0 = ws + cx.off_b0;
+      for (int64_t idx = tid; idx < tot; idx += blockDim.x) {
+        int64_t rem = idx, src = 0, strd = 1;
+        for (int n = p - 1; n >= 0; --n) {
+          const int in = (int)(rem % dims[n]);
+          rem /= dims[n];
+          src += in * strd;
+          strd *= tv.r[n];
+        }
+        b0[idx] = core[src];
+      }
+      // clean upper-triangular R~ (q0 x nr0) into W
+      S* Rt = ws + cx.off_W;
+      const int q0 = h.q[0];
+      for (int idx = tid; idx < q0 * nr0; idx += blockDim.x) {
+        const int a = idx / nr0, b = idx % nr0;
+        Rt[idx] = (b >= a) ? sl[a * nr0 + b] : S(0);
+      }
+      __syncthreads();
+      ttm<S>(b0, dims, p, 0, Rt, nr0, 1, q0, Hc, false);
+    }
+    int64_t tot = 1;
+    for (int n = 0; n < p; ++n) tot *= h.q[n];
+    hn2 += sum_squares<S>(Hc, tot, sm.red);
+  }
+
+  // ---- non-temporal bases Phi_n = Q_n R_n, and the implicit HOSVD start ---
+  for (int n = 1; n < p; ++n) {
+    const int Dn = tv.D[n], kn = cx.k[n], cn = cx.c[n];
+    S* Phi = ws + cx.off_phi[n];
+    for (int i = 0; i < nh; ++i) {
+      const HitRec& h = hits[i];
+      const S* F = reinterpret_cast<const S*>(tv.fac_pool[n]) + h.slot * tv.fac_stride[n];
+      const int qn = h.q[n];
+      for (int idx = tid; idx < Dn * qn; idx += blockDim.x) {
+        const int d = idx / qn, c = idx % qn;
+        Phi[(int64_t)d * kn + h.koff[n] + c] = F[(int64_t)d * tv.r[n] + c];
+      }
+    }
+    __syncthreads();
+    householder_qr<S>(Phi, Dn, kn, kn, ws + cx.off_tau[n], sm.sc);
+    S* R = ws + cx.off_R[n];
+    for (int idx = tid; idx < cn * kn; idx += blockDim.x) {
+      const int a = idx / kn, b = idx % kn;
+      R[idx] = (b >= a) ? Phi[(int64_t)a * kn + b] : S(0);
+    }
+    for (int idx = tid; idx < cn * cn; idx += blockDim.x) A[(idx / cn) * cn + idx % cn] = 0;
+    __syncthreads();
+    // init: sum_i modegram_n(H~_i x_n R_n[:, blk i]) = Q_n^T mat_n(Y~) mat_n(Y~)^T Q_n
+    for (int i = 0; i < nh; ++i) {
+      const HitRec& h = hits[i];
+      for (int m = 0; m < p; ++m) dims[m] = h.q[m];
+      S* b0 = ws + cx.off_b0;
+      ttm<S>(ws + h.core_off, dims, p, n, R + h.koff[n], kn, 1, cn, b0, false);
+      dims[n] = cn;
+      mode_gram<S>(b0, dims, p, n, A, cn, true);
+    }
+    jacobi_eig<S>(cn, A, cn, V, cn, wv, js_cs, js, sm.red, maxsw);
+    select_top<S>(cn, wv, V, cn, cx.ro[n], ws + cx.off_E[n], cx.ro[n]);
+  }
+
+  // ---- Algorithm 2 iterations --------------------------------------------
+  S e_prev = S(-1);
+  S e = 0;
+  int it = 0;
+  const int maxit = tv.max_iter > 0 ? tv.max_iter : 1;
+  const int* ro = cx.ro;
+  S* K = ws + cx.off_K;
+  S* C = ws + cx.off_E[0];
+  S* N = ws + cx.off_N;
+  S* Wb = ws + cx.off_W;
+  S* b0 = ws + cx.off_b0;
+  S* b1 = ws + cx.off_b1;
+  for (it = 1; it <= maxit; ++it) {
+    // temporal mode, Eq. (stitch-temp-2) in coefficient space
+    int64_t krow = 1;
+    for (int m = 1; m < p; ++m) krow *= ro[m];
+    for (int i = 0; i < nh; ++i) {
+      const HitRec& h = hits[i];
+      for (int m = 0; m < p; ++m) dims[m] = h.q[m];
+      const S* src = ws + h.core_off;
+      for (int m = 1; m < p; ++m) {
+        proj_coef<S>(ws + cx.off_E[m], cx.c[m], ro[m], ws + cx.off_R[m], cx.k[m], h.koff[m], h.q[m], Wb);
+        S* dst = (m == p - 1) ? K + (int64_t)h.koff[0] * krow : ((m & 1) ? b0 : b1);
+        ttm<S>(src, dims, p, m, Wb, h.q[m], 1, ro[m], dst, false);
+        dims[m] = ro[m];
+        src = dst;
+      }
+    }
+    {
+      const int c0 = cx.c[0];
+      dims[0] = c0;
+      for (int m = 1; m < p; ++m) dims[m] = ro[m];
+      mode_gram<S>(K, dims, p, 0, A, c0, false);
+      jacobi_eig<S>(c0, A, c0, V, c0, wv, js_cs, js, sm.red, maxsw);
+      select_top<S>(c0, wv, V, c0, ro[0], C, ro[0]);
+    }
+    // non-temporal modes, Eq. (stitch-nontemp-3) in coefficient space
+    for (int n = 1; n < p; ++n) {
+      const int cn = cx.c[n], kn = cx.k[n];
+      for (int i = 0; i < nh; ++i) {
+        const HitRec& h = hits[i];
+        for (int m = 0; m < p; ++m) dims[m] = h.q[m];
+        // x_1 C_i^T : M(alpha, j) = C[(koff0 + j) * ro0 + alpha]
+        ttm<S>(ws + h.core_off, dims, p, 0, C + (int64_t)h.koff[0] * ro[0], 1, ro[0], ro[0], b0, false);
+        dims[0] = ro[0];
+        S* src = b0;
+        S* other = b1;
+        for (int m = 1; m < p; ++m) {
+          if (m == n) continue;
+          proj_coef<S>(ws + cx.off_E[m], cx.c[m], ro[m], ws + cx.off_R[m], cx.k[m], h.koff[m], h.q[m], Wb);
+          ttm<S>(src, dims, p, m, Wb, h.q[m], 1, ro[m], other, false);
+          dims[m] = ro[m];
+          S* t = src;
+          src = other;
+          other = t;
+        }
+        ttm<S>(src, dims, p, n, ws + cx.off_R[n] + h.koff[n], kn, 1, cn, N, i > 0);
+      }
+      for (int m = 0; m < p; ++m) dims[m] = ro[m];
+      dims[n] = cn;
+      mode_gram<S>(N, dims, p, n, A, cn, false);
+      jacobi_eig<S>(cn, A, cn, V, cn, wv, js_cs, js, sm.red, maxsw);
+      select_top<S>(cn, wv, V, cn, ro[n], ws + cx.off_E[n], ro[n]);
+    }
+    // core: G = N_p x_p E_p^T (Algorithm 2's last step) and the stop test
+    {
+      const int n = p - 1;
+      for (int m = 0; m < p; ++m) dims[m] = ro[m];
+      dims[n] = cx.c[n];
+      ttm<S>(N, dims, p, n, ws + cx.off_E[n], 1, ro[n], ro[n], ws + cx.off_G, false);
+    }
+    int64_t gel = 1;
+    for (int m = 0; m < p; ++m) gel *= ro[m];
+    const S gn2 = sum_squares<S>(ws + cx.off_G, gel, sm.red);
+    e = hn2 > S(0) ? sqrt(fmax(S(0), S(1) - gn2 / hn2)) : S(0);
+    if (tv.tol > 0 && it > 1 && fabs(e - e_prev) < (S)tv.tol) break;
+    e_prev = e;
+  }
+  if (it > maxit) it = maxit;
+
+  // ---- outputs: core, U^(1) = blockdiag(V~_i^(1)) C, U^(n) = Q_n E_n --------
+  {
+    int64_t ctot = 1, gel = 1;
+    for (int m = 0; m < p; ++m) {
+      ctot *= rq[m];
+      gel *= ro[m];
+    }
+    const S* G = ws + cx.off_G;
+    for (int64_t idx = tid; idx < ctot; idx += blockDim.x) {
+      int64_t rem = idx, src = 0, strd = 1;
+      bool inside = true;
+      for (int n = p - 1; n >= 0; --n) {
+        const int in = (int)(rem % rq[n]);
+        rem /= rq[n];
+        if (in >= ro[n]) inside = false;
+        src += in * strd;
+        strd *= ro[n];
+      }
+      core_dst[idx] = inside ? G[src] : S(0);
+    }
+  }
+  for (int i = 0; i < nh; ++i) {
+    const HitRec& h = hits[i];
+    const int64_t ell = h.hi - h.lo;
+    S* Y = u0_dst + h.toff * ld0;
+    const S* Ci = C + (int64_t)h.koff[0] * ro[0];
+    if (!h.partial) {
+      const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride + h.lo * tv.r[0];
+      gemm<S>((int)ell, ro[0], h.q[0], tf, tv.r[0], 1, Ci, ro[0], 1, Y, ld0, 1, false);
+    } else {
+      for (int64_t idx = tid; idx < ell * ro[0]; idx += blockDim.x) {
+        const int64_t t = idx / ro[0];
+        const int a = (int)(idx % ro[0]);
+        Y[t * ld0 + a] = (t < h.q[0]) ? Ci[t * ro[0] + a] : S(0);
+      }
+      __syncthreads();
+      householder_apply_q<S>(ws + h.slice_off, (int)ell, h.q[0], h.nr0, ws + h.stau_off, Y, ro[0], ld0);
+    }
+    if (ro[0] < rq[0]) {
+      const int padc = rq[0] - ro[0];
+      for (int64_t idx = tid; idx < ell * padc; idx += blockDim.x) Y[(idx / padc) * ld0 + ro[0] + idx % padc] = 0;
+    }
+    __syncthreads();
+  }
+  for (int n = 1; n < p; ++n) {
+    const int Dn = tv.D[n], cn = cx.c[n];
+    S* Y = un_dst[n];
+    const int64_t ld = ldn[n];
+    const S* E = ws + cx.off_E[n];
+    for (int64_t idx = tid; idx < (int64_t)Dn * rq[n]; idx += blockDim.x) {
+      const int d = (int)(idx / rq[n]), a = (int)(idx % rq[n]);
+      Y[d * ld + a] = (a < ro[n] && d < cn) ? E[d * ro[n] + a] : S(0);
+    }
+    __syncthreads();
+    householder_apply_q<S>(ws + cx.off_phi[n], Dn, cn, cx.k[n], ws + cx.off_tau[n], Y, ro[n], ld);
+  }
+  if (tid == 0) {
+    if (ranks_dst)
+      for (int n = 0; n < TK_MAXP; ++n) ranks_dst[n] = n < p ? ro[n] : 0;
+    if (info) {
+      for (int n = 0; n < TK_MAXP; ++n) info->ranks[n] = n < p ? ro[n] : 0;
+      info->iters = it;
+      info->n_hits = nh;
+      info->fit_err = (double)e;
+    }
+  }
+  __syncthreads();
+}
+
+template <class S>
+__global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int level, int64_t k0, int njobs,
+                                                  TkQueryBatch qb, TkWorkspace wsd) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
+  for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
+    if (mode == TK_JOB_QUERY) {
+      const int64_t ts = qb.ranges[2 * job], te = qb.ranges[2 * job + 1];
+      S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[job];
+      tk_query_info* info = qb.info ? qb.info + job : nullptr;
+      if (!(ts >= 0 && ts < te && te <= tv.T)) {
+        if (threadIdx.x == 0) {
+          set_err(wsd.status, TK_DEV_ERR_RANGE);
+          if (info) info->iters = -TK_DEV_ERR_RANGE;
+        }
+        continue;
+      }
+      int64_t ctot = 1;
+      for (int n = 0; n < tv.p; ++n) ctot *= qb.rq[n];
+      S* u0 = out + ctot;
+      S* un[TK_MAXP];
+      int64_t ldn[TK_MAXP];
+      S* cur = u0 + (te - ts) * qb.rq[0];
+      for (int n = 1; n < tv.p; ++n) {
+        un[n] = cur;
+        ldn[n] = qb.rq[n];
+        cur += (int64_t)tv.D[n] * qb.rq[n];
+      }
+      stitch_job<S>(tv, mode, ts, te, 0, 0, qb.rq, ws, wsd.per_cta, wsd.nsm, out, u0, qb.rq[0], un, ldn,
+                    nullptr, info, wsd.status, smem_raw);
+    } else {
+      const int64_t k = k0 + job;
+      const int64_t slot = tv.level_base[level] + k;
+      S* core = reinterpret_cast<S*>(tv.core_pool) + slot * tv.core_stride;
+      S* u0 = reinterpret_cast<S*>(tv.tfac) + level * tv.tfac_level_stride + node_lo_of(tv, level, k) * tv.r[0];
+      S* un[TK_MAXP];
+      int64_t ldn[TK_MAXP];
+      for (int n = 1; n < tv.p; ++n) {
+        un[n] = reinterpret_cast<S*>(tv.fac_pool[n]) + slot * tv.fac_stride[n];
+        ldn[n] = tv.r[n];
+      }
+      stitch_job<S>(tv, mode, 0, 0, level, k, tv.r, ws, wsd.per_cta, wsd.nsm, core, u0, tv.r[0], un, ldn,
+                    tv.node_ranks + slot * TK_MAXP, nullptr, wsd.status, smem_raw);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- leaf blocks: Tucker-ALS of Section 2 on the raw block ---------------
+template <class S>
+__global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int64_t block_stride,
+                                                int64_t first_block, int njobs, int ell, TkWorkspace wsd) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  struct LeafSm {
+    S red[40];
+    S sc[4];
+    int flag;
+    int rl[TK_MAXP];
+    int64_t off_U[TK_MAXP], off_b0, off_b1, off_G, off_A, off_V, off_w, off_cs, off_pq;
+    int err, eig_in_smem;
+  };
+  static_assert(sizeof(LeafSm) <= 512, "leaf shared header");
+  LeafSm& sm = *reinterpret_cast<LeafSm*>(smem_raw);
+  const int nsm = wsd.nsm;
+  const int half_cap = nsm / 2 + 2;
+  int* js_pq = reinterpret_cast<int*>(smem_raw + ((sizeof(LeafSm) + 15) & ~(size_t)15));
+  S* js_cs = reinterpret_cast<S*>(((uintptr_t)(js_pq + half_cap) + 15) & ~(uintptr_t)15);
+  S* js_w = js_cs + 2 * half_cap;
+  S* sA = js_w + nsm + 2;
+  S* sV = sA + (int64_t)nsm * nsm;
+  S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
+  const int p = tv.p;
+  const int tid = threadIdx.x;
+  const int maxsw = sizeof(S) == 8 ? 24 : 16;
+  for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
+    const int64_t b = first_block + job;
+    const S* X = raw + (int64_t)job * block_stride;
+    const int64_t slot = tv.level_base[0] + b;
+    int xd[TK_MAXP];
+    xd[0] = ell;
+    for (int n = 1; n < p; ++n) xd[n] = tv.D[n];
+    if (tid == 0) {
+      // rank clamp: min(r_n, extent_n), then r_n <= prod_{m!=n} r_m
+      for (int n = 0; n < p; ++n) sm.rl[n] = tv.r[n] < xd[n] ? tv.r[n] : xd[n];
+      bool ch = true;
+      while (ch) {
+        ch = false;
+        for (int n = 0; n < p; ++n) {
+          int64_t pr = 1;
+          for (int m = 0; m < p; ++m)
+            if (m != n) pr *= sm.rl[m];
+          if (sm.rl[n] > pr) {
+            sm.rl[n] = (int)pr;
+            ch = true;
+          }
+        }
+      }
+      int64_t cur = 0;
+      auto take = [&](int64_t nel) {
+        const int64_t o = cur;
+        cur += (nel + 31) & ~(int64_t)31;
+        return o;
+      };
+      int neig = 0;
+      for (int n = 0; n < p; ++n) {
+        sm.off_U[n] = take((int64_t)xd[n] * sm.rl[n]);
+        if (xd[n] > neig) neig = xd[n];
+      }
+      int64_t xel = 1;
+      for (int n = 0; n < p; ++n) xel *= xd[n];
+      sm.off_b0 = take(xel);
+      sm.off_b1 = take(xel);
+      int64_t gel = 1;
+      for (int n = 0; n < p; ++n) gel *= sm.rl[n];
+      sm.off_G = take(gel);
+      sm.eig_in_smem = neig <= nsm;
+      if (!sm.eig_in_smem) {
+        sm.off_A = take((int64_t)neig * neig);
+        sm.off_V = take((int64_t)neig * neig);
+        sm.off_w = take(neig + 2);
+        sm.off_cs = take(2 * (neig / 2 + 2));
+        sm.off_pq = take(((neig / 2 + 2) * (int64_t)sizeof(int) + sizeof(S) - 1) / sizeof(S));
+      }
+      sm.err = cur > wsd.per_cta ? TK_DEV_ERR_WORKSPACE : 0;
+    }
+    __syncthreads();
+    if (sm.err) {
+      if (tid == 0) set_err(wsd.status, sm.err);
+      continue;
+    }
+    int rl[TK_MAXP];
+    for (int n = 0; n < p; ++n) rl[n] = sm.rl[n];
+    S* A = sm.eig_in_smem ? sA : ws + sm.off_A;
+    S* V = sm.eig_in_smem ? sV : ws + sm.off_V;
+    S* ew = sm.eig_in_smem ? js_w : ws + sm.off_w;
+    S* ecs = sm.eig_in_smem ? js_cs : ws + sm.off_cs;
+    JacobiScratch ejs{sm.eig_in_smem ? js_pq : reinterpret_cast<int*>(ws + sm.off_pq), &sm.flag};
+    S* b0 = ws + sm.off_b0;
+    S* b1 = ws + sm.off_b1;
+    int64_t xel = 1;
+    for (int n = 0; n < p; ++n) xel *= xd[n];
+    const S xn2 = sum_squares<S>(X, xel, sm.red);
+    int dims[TK_MAXP];
+    // HOSVD start for modes 2..p
+    for (int n = 1; n < p; ++n) {
+      mode_gram<S>(X, xd, p, n, A, xd[n], false);
+      jacobi_eig<S>(xd[n], A, xd[n], V, xd[n], ew, ecs, ejs, sm.red, maxsw);
+      select_top<S>(xd[n], ew, V, xd[n], rl[n], ws + sm.off_U[n], rl[n]);
+    }
+    S e_prev = S(-1), e = 0;
+    int it;
+    const int maxit = tv.max_iter > 0 ? tv.max_iter : 1;
+    for (it = 1; it <= maxit; ++it) {
+      for (int n = 0; n <= p; ++n) {  // n == p: the core
+        const S* src = X;
+        for (int m = 0; m < p; ++m) dims[m] = xd[m];
+        bool first = true;
+        for (int m = p - 1; m >= 0; --m) {
+          if (m == n) continue;
+          S* dst;
+          if (n == p && m == 0) dst = ws + sm.off_G;
+          else dst = first ? b0 : (src == b0 ? b1 : b0);
+          ttm<S>(src, dims, p, m, ws + sm.off_U[m], 1, rl[m], rl[m], dst, false);
+          dims[m] = rl[m];
+          src = dst;
+          first = false;
+        }
+        if (n == p) break;
+        mode_gram<S>(src, dims, p, n, A, xd[n], false);
+        jacobi_eig<S>(xd[n], A, xd[n], V, xd[n], ew, ecs, ejs, sm.red, maxsw);
+        select_top<S>(xd[n], ew, V, xd[n], rl[n], ws + sm.off_U[n], rl[n]);
+      }
+      int64_t gel = 1;
+      for (int m = 0; m < p; ++m) gel *= rl[m];
+      const S gn2 = sum_squares<S>(ws + sm.off_G, gel, sm.red);
+      e = xn2 > S(0) ? sqrt(fmax(S(0), S(1) - gn2 / xn2)) : S(0);
+      if (tv.tol > 0 && it > 1 && fabs(e - e_prev) < (S)tv.tol) break;
+      e_prev = e;
+    }
+    // store: core (capacity dims r), temporal rows (ld r0), factors (ld r_n)
+    {
+      S* core = reinterpret_cast<S*>(tv.core_pool) + slot * tv.core_stride;
+      int64_t ctot = 1;
+      for (int m = 0; m < p; ++m) ctot *= tv.r[m];
+      const S* G = ws + sm.off_G;
+      for (int64_t idx = tid; idx < ctot; idx += blockDim.x) {
+        int64_t rem = idx, src = 0, strd = 1;
+        bool inside = true;
+        for (int n = p - 1; n >= 0; --n) {
+          const int in = (int)(rem % tv.r[n]);
+          rem /= tv.r[n];
+          if (in >= rl[n]) inside = false;
+          src += in * strd;
+          strd *= rl[n];
+        }
+        core[idx] = inside ? G[src] : S(0);
+      }
+      S* tf = reinterpret_cast<S*>(tv.tfac) + b * (int64_t)tv.B * tv.r[0];
+      const S* U0 = ws + sm.off_U[0];
+      for (int64_t idx = tid; idx < (int64_t)ell * tv.r[0]; idx += blockDim.x) {
+        const int64_t t = idx / tv.r[0];
+        const int c = (int)(idx % tv.r[0]);
+        tf[idx] = c < rl[0] ? U0[t * rl[0] + c] : S(0);
+      }
+      for (int n = 1; n < p; ++n) {
+        S* F = reinterpret_cast<S*>(tv.fac_pool[n]) + slot * tv.fac_stride[n];
+        const S* Un = ws + sm.off_U[n];
+        for (int64_t idx = tid; idx < (int64_t)tv.D[n] * tv.r[n]; idx += blockDim.x) {
+          const int64_t d = idx / tv.r[n];
+          const int c = (int)(idx % tv.r[n]);
+          F[idx] = c < rl[n] ? Un[d * rl[n] + c] : S(0);
+        }
+      }
+      if (tid < TK_MAXP) tv.node_ranks[slot * TK_MAXP + tid] = tid < p ? rl[tid] : 0;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_hitset(TkTreeView tv, int n, const int64_t* ranges, tk_hit* out, int cap, int* counts) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  HitRec hits[TK_MAXH];
+  const int nh = recall_dev(tv, ranges[2 * q], ranges[2 * q + 1], hits, TK_MAXH);
+  counts[q] = nh;
+  for (int i = 0; i < nh && i < cap; ++i) {
+    tk_hit& o = out[(int64_t)q * cap + i];
+    o.level = hits[i].level;
+    o.partial = hits[i].partial;
+    o.index = hits[i].index;
+    o.node_lo = hits[i].node_lo;
+    o.node_hi = hits[i].node_hi;
+    o.lo = hits[i].lo;
+    o.hi = hits[i].hi;
+  }
+}
+
+}  // namespace tk
+
+using namespace tk;
+
+static size_t stitch_smem(size_t es, int nsm) {
+  const int half_cap = nsm / 2 + 2;
+  size_t fixed = offsetof(Smem<double>, pq);
+  if (es == 4) fixed = offsetof(Smem<float>, pq);
+  size_t b = fixed + half_cap * sizeof(int);
+  b = (b + 15) & ~(size_t)15;
+  b += es * (2 * half_cap + nsm + 2 + 2 * (size_t)nsm * nsm);
+  return b + 64;
+}
+
+static size_t leaf_smem(size_t es, int nsm) {
+  const int half_cap = nsm / 2 + 2;
+  size_t fixed = 512;  // LeafSm (< 512 bytes), rounded
+  size_t b = fixed + half_cap * sizeof(int);
+  b = (b + 15) & ~(size_t)15;
+  b += es * (2 * half_cap + nsm + 2 + 2 * (size_t)nsm * nsm);
+  return b + 64;
+}
+
+size_t tk_stitch_smem_bytes(int dtype, int nsm) { return stitch_smem(dtype == TK_F64 ? 8 : 4, nsm); }
+size_t tk_leaf_smem_bytes(int dtype, int nsm) { return leaf_smem(dtype == TK_F64 ? 8 : 4, nsm); }
+
+template <class S> static const void* stitch_fn() { return (const void*)k_stitch<S>; }
+template <class S> static const void* leaf_fn() { return (const void*)k_leaf<S>; }
+
+static int set_smem_attr(const void* fn, size_t smem) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return TK_ERR_CUDA;
+  return TK_OK;
+}
+
+int tk_occupancy(int dtype, int which, size_t smem) {
+  const void* fn = which == 0 ? (dtype == TK_F64 ? leaf_fn<double>() : leaf_fn<float>())
+                              : (dtype == TK_F64 ? stitch_fn<double>() : stitch_fn<float>());
+  if (set_smem_attr(fn, smem) != TK_OK) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TK_NT, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t block_stride, int64_t first_block,
+                   int njobs, int ell, const TkWorkspace& ws, int grid, cudaStream_t stream) {
+  if (njobs <= 0) return TK_OK;
+  const size_t smem = tk_leaf_smem_bytes(dtype, ws.nsm);
+  if (dtype == TK_F64) {
+    if (set_smem_attr(leaf_fn<double>(), smem)) return TK_ERR_CUDA;
+    k_leaf<double><<<grid, TK_NT, smem, stream>>>(tv, (const double*)raw, block_stride, first_block, njobs, ell, ws);
+  } else {
+    if (set_smem_attr(leaf_fn<float>(), smem)) return TK_ERR_CUDA;
+    k_leaf<float><<<grid, TK_NT, smem, stream>>>(tv, (const float*)raw, block_stride, first_block, njobs, ell, ws);
+  }
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+}
+
+int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int njobs, const TkWorkspace& ws,
+                    int grid, cudaStream_t stream) {
+  if (njobs <= 0) return TK_OK;
+  const size_t smem = tk_stitch_smem_bytes(dtype, ws.nsm);
+  TkQueryBatch qb{};
+  if (dtype == TK_F64) {
+    if (set_smem_attr(stitch_fn<double>(), smem)) return TK_ERR_CUDA;
+    k_stitch<double><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_MERGE, level, k0, njobs, qb, ws);
+  } else {
+    if (set_smem_attr(stitch_fn<float>(), smem)) return TK_ERR_CUDA;
+    k_stitch<float><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_MERGE, level, k0, njobs, qb, ws);
+  }
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+}
+
+int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, const TkWorkspace& ws, int grid,
+                    cudaStream_t stream) {
+  if (qb.n <= 0) return TK_OK;
+  const size_t smem = tk_stitch_smem_bytes(dtype, ws.nsm);
+  if (dtype == TK_F64) {
+    if (set_smem_attr(stitch_fn<double>(), smem)) return TK_ERR_CUDA;
+    k_stitch<double><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws);
+  } else {
+    if (set_smem_attr(stitch_fn<float>(), smem)) return TK_ERR_CUDA;
+    k_stitch<float><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws);
+  }
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+}
+
+int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap, int* counts,
+                     cudaStream_t stream) {
+  if (n <= 0) return TK_OK;
+  const int nt = 32;
+  k_hitset<<<(n + nt - 1) / nt, nt, 0, stream>>>(tv, n, ranges, out, cap, counts);
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+}
