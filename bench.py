@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Range-query throughput of the GPU engine on the FP32 plain workload.
+
+One step = one batched launch answering the workload's 1000 range queries
+(Recall, partial-hit QR, Stitch/HOOI, factor assembly: every row of the hot
+path) over a tree already resident in HBM.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the literal restatement of the
+paper's algorithms) on the host cores instead, on bounded samples of the same
+workload.  Multi-GPU runs are replicas (every rank holds the tree and answers
+its own copy of the query batch; no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "range queries/sec + p50/p99 query latency at matched recon error vs plain"
+UNIT = "queries/s"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_desc(w):
+    return (f"fp32_plain: {w['dims'][0]}x{w['dims'][1]}xT={w['T']} piecewise Tucker rank-{tuple(w['ranks'])}, "
+            f"regime {w['regime']}, sigma {w['sigma']}, leaf {w['B']} slices, {w['n_queries']} log-uniform "
+            f"queries L in [{w['lo']},{w['hi']}], theta 0.7, max_iter 20, tol 0.01")
+
+
+# ---------------------------------------------------------------------------
+# algorithmic FLOPs of one query in the coefficient-space form
+# ---------------------------------------------------------------------------
+def query_flops(hits, ranks_out, node_ranks, dims, iters):
+    """FLOPs of one range query: partial-hit QR, QR of the stacked factors,
+    initial Gram/eig, `iters` ALS iterations (TTM chains, Grams, eigs at the
+    textbook 9n^3), the core, and the assembly of U1..Up."""
+    p = len(ranks_out)
+    ro = list(ranks_out)
+    q = []
+    f = 0.0
+    for (level, index, lo_n, hi_n, lo, hi, partial) in hits:
+        qi = list(node_ranks)
+        ell = hi - lo
+        if partial:
+            qi[0] = min(ell, node_ranks[0])
+            n = node_ranks[0]
+            f += 2.0 * ell * n * n - 2.0 / 3.0 * min(ell, n) ** 3        # Householder QR
+            f += 2.0 * qi[0] * np.prod(node_ranks)                        # core x_1 R
+        q.append(qi)
+    k = [sum(qi[n] for qi in q) for n in range(p)]
+    c = [k[0]] + [min(dims[n - 1], k[n]) for n in range(1, p)]
+    eig = lambda n: 9.0 * n ** 3
+    for n in range(1, p):
+        Dn = dims[n - 1]
+        f += 2.0 * Dn * k[n] ** 2 - 2.0 / 3.0 * min(Dn, k[n]) ** 3      # QR of Phi_n
+        for qi in q:
+            rest = np.prod(qi) / qi[n]
+            f += 2.0 * c[n] * qi[n] * rest + 2.0 * c[n] ** 2 * rest       # x_n R, Gram
+        f += eig(c[n])
+
+    def chain(qi, order_dims, modes):
+        fl, d = 0.0, list(order_dims)
+        for m, a in modes:
+            fl += 2.0 * np.prod(d) * a
+            d[m] = a
+        return fl
+
+    for _ in range(iters):
+        R0 = np.prod(ro[1:])
+        for qi in q:
+            for m in range(1, p):
+                f += 2.0 * ro[m] * qi[m] * c[m]                           # W_im
+            f += chain(qi, qi, [(m, ro[m]) for m in range(1, p)])
+        f += 2.0 * k[0] ** 2 * R0 + eig(c[0])
+        for n in range(1, p):
+            for qi in q:
+                modes = [(0, ro[0])] + [(m, ro[m]) for m in range(1, p) if m != n] + [(n, c[n])]
+                for m in range(1, p):
+                    if m != n:
+                        f += 2.0 * ro[m] * qi[m] * c[m]
+                f += chain(qi, qi, modes)
+            Rn = np.prod(ro) / ro[n]
+            f += 2.0 * c[n] ** 2 * Rn + eig(c[n])
+        f += 2.0 * np.prod(ro) * c[p - 1]                                  # core
+    for qi, (level, index, lo_n, hi_n, lo, hi, partial) in zip(q, hits):
+        ell = hi - lo
+        f += (4.0 if partial else 2.0) * ell * qi[0] * ro[0]               # U1 rows
+    for n in range(1, p):
+        f += 4.0 * dims[n - 1] * c[n] * ro[n]                              # Q_n E_n
+    return f
+
+
+# ---------------------------------------------------------------------------
+# FP64 CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+_ORACLE = None
+
+
+def _oracle_init(tree):
+    global _ORACLE
+    _ORACLE = tree
+
+
+def _oracle_query(args):
+    ts, te = args
+    t0 = time.perf_counter()
+    r = _ORACLE.query(int(ts), int(te))
+    return time.perf_counter() - t0, r["G"], r["U"], r["iters"]
+
+
+def build_oracle_tree(w, X):
+    from oracle.tree import StreamSegmentTree
+    t = StreamSegmentTree(w["dims"], w["ranks"], B=w["B"], max_iter=20, tol=0.01)
+    t.build(X)
+    return t
+
+
+def oracle_pool(tree, cores):
+    """Spawned workers (BLAS single-threaded), each holding the oracle tree."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(cores, initializer=_oracle_init, initargs=(tree,))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    X = synth.piecewise_tucker(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
+    tree = build_oracle_tree(w, X)
+    cores = host_cores()
+    per_step = 64
+    with oracle_pool(tree, cores) as pool:
+        pool.map(_oracle_query, [tuple(Q[0])] * cores)
+        times = []
+        for s in range(args.warmup + args.steps):
+            idx = [(s * per_step + j) % len(Q) for j in range(per_step)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_query, [tuple(Q[i]) for i in idx], chunksize=1)
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append(dt)
+    total = sum(times)
+    value = per_step * len(times) / total
+    sample = f"{per_step} queries of the workload per step (cycling through its {len(Q)} queries), process pool"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "impl_note": "FP64 NumPy/LAPACK oracle of the paper's algorithms"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fp32_plain")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = synth.WORKLOADS[args.workload]
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_2501_06647_gb300 as tk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    X = synth.piecewise_tucker(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
+    stream = torch.cuda.Stream(device=dev)
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32",
+                   device=local, stream=stream)
+    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    tree.build(Xd)
+    tree.sync()
+    build_s = time.perf_counter() - tb0
+    del Xd
+
+    offsets = tree.layout(Q)
+    ranges_d = torch.from_numpy(Q.copy()).to(dev)
+    offsets_d = torch.from_numpy(offsets).to(dev)
+    out_d = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        tree.query_batch(ranges_d, offsets_d, out_d)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+    tree.sync()
+
+    # ---- timed region (device time of the query launches; L2 flushed between) --
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = tree.launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    gpu_launches = tree.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    n_q = len(Q)
+    value = world * n_q * args.steps / (total_ms / 1e3)
+    tree.sync()
+
+    # ---- per-query latency: one query per launch (plain method) ------------------
+    lat = []
+    one_off = tree.layout(Q[:1])
+    with torch.cuda.stream(stream):
+        for i in range(200):
+            r = torch.from_numpy(Q[i:i + 1].copy()).to(dev)
+            o = torch.from_numpy(tree.layout(Q[i:i + 1])).to(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.query_batch(r, o, out_d)
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+    del one_off
+    lat_sorted = sorted(lat)
+    p50 = lat_sorted[len(lat) // 2]
+    p99 = lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    host_out = torch.empty(int(offsets[-1]), dtype=torch.float32, pin_memory=True).numpy()
+    host_ranges = torch.from_numpy(Q.copy()).pin_memory().numpy()
+    host_offs = torch.from_numpy(offsets.copy()).pin_memory().numpy()
+    tree.query_batch_host(host_ranges, host_offs, host_out, with_info=False)
+    e2e_s = 0.0
+    e2e_steps = max(3, args.steps)
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree.query_batch_host(host_ranges, host_offs, host_out, with_info=False)
+        e2e_s += time.perf_counter() - t0
+    e2e_value = world * n_q * e2e_steps / e2e_s
+
+    # ---- roofline of the dominant kernel (the batched stitch launch) -------------
+    info = (tk.TkQueryInfo * n_q)()
+    out_chk, _, info = tree.query_batch_host(Q, offsets, None, with_info=True)
+    flops = 0.0
+    for i, (ts, te) in enumerate(Q):
+        hits = tree.hit_set(int(ts), int(te))
+        ro = list(info[i].ranks[: tree.p])
+        flops += query_flops(hits, ro, list(w["ranks"]), list(w["dims"]), int(info[i].iters))
+    avg_launch_s = total_ms / 1e3 / args.steps
+    achieved = flops / avg_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_stitch<float> (one launch answers the whole batch)",
+                "flops_per_launch": flops,
+                "peak_note": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "queries_per_step": n_q,
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "tree_build_s": build_s, "tree_arena_bytes": tree.arena_bytes()},
+        "latency_ms": {"p50": p50, "p99": p99, "mode": "one query per launch (plain method), 200 queries"},
+        "batch_latency_ms": total_ms / args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Q.nbytes + offsets.nbytes),
+                "d2h_bytes_per_step": int(offsets[-1]) * 4},
+        "gpu_launches": gpu_launches,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
+
+    # ---- FP64 oracle on the host cores: cpu_baseline + matched-error check -------
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu_section(line, w, X, Q, offsets, tree, out_chk, info, n_q)
+        except Exception as exc:  # report, do not lose the GPU measurement
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                                    "sample": None, "error": f"{type(exc).__name__}: {exc}"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    tree.close()
+    return 0
+
+
+def cpu_section(line, w, X, Q, offsets, tree, out_chk, info, n_q):
+    """FP64 oracle on the host cores: cpu_baseline and the matched-error check."""
+    tree_o = build_oracle_tree(w, X)
+    cores = host_cores()
+    sample = list(range(0, n_q, max(1, n_q // 400)))[:400]
+    with oracle_pool(tree_o, cores) as pool:
+        pool.map(_oracle_query, [tuple(Q[0])] * cores)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_query, [tuple(Q[i]) for i in sample], chunksize=1)
+        wall = time.perf_counter() - t0
+    line["cpu_baseline"] = {"value": len(sample) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{len(sample)} of the {n_q} workload queries (every "
+                                      f"{max(1, n_q // 400)}th), tree prebuilt, process pool, "
+                                      "BLAS single-threaded per worker"}
+    from oracle import metrics
+    eg, eo, dd = [], [], []
+    for j, i in enumerate(sample[:100]):
+        ts, te = int(Q[i][0]), int(Q[i][1])
+        G, U = tree.unpack(out_chk[offsets[i]:offsets[i + 1]], te - ts)
+        r = list(info[i].ranks[: tree.p])
+        G = np.float64(G[tuple(slice(0, x) for x in r)])
+        U = [np.float64(u[:, :x]) for u, x in zip(U, r)]
+        Xs = X[ts:te]
+        eg.append(metrics.relative_error(Xs, G, U))
+        eo.append(metrics.relative_error(Xs, res[j][1], res[j][2]))
+        dd.append(metrics.model_distance(G, U, res[j][1], res[j][2]) / np.linalg.norm(Xs))
+    line["accuracy"] = {"queries": len(eg), "mean_rel_err_gpu": float(np.mean(eg)),
+                        "mean_rel_err_oracle_fp64": float(np.mean(eo)),
+                        "max_abs_err_diff": float(np.max(np.abs(np.array(eg) - np.array(eo)))),
+                        "max_model_distance_rel": float(np.max(dd)),
+                        "note": "both with tol 0.01; iteration counts may differ near the threshold"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

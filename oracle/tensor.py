@@ -56,9 +56,17 @@ def frob(X):
 def leading_left_singular_vectors(M, r):
     """The r leading left singular vectors of M (Section 2, Eq. (als-mat)).
 
-    LAPACK's SVD is the library step.  Only the spanned subspace is unique.
+    LAPACK's SVD is the library step (divide and conquer, gesdd; if that
+    driver reports non-convergence, which some LAPACK builds do on rare
+    inputs, the same SVD is taken with the QR-iteration driver gesvd).  Only
+    the spanned subspace is unique.
     """
-    U, _, _ = np.linalg.svd(np.asarray(M, dtype=np.float64), full_matrices=False)
+    M = np.asarray(M, dtype=np.float64)
+    try:
+        U, _, _ = np.linalg.svd(M, full_matrices=False)
+    except np.linalg.LinAlgError:
+        import scipy.linalg
+        U, _, _ = scipy.linalg.svd(M, full_matrices=False, lapack_driver="gesvd")
     return U[:, :r].copy()
 
 

@@ -11,8 +11,10 @@ Readings (listed in DESIGN.md):
     a leaf's payload is Tucker-ALS (``hooi.tucker_als``) of its raw block.
   * Open block.  When the first slice of block b arrives, Algorithm 4 (root
     extension) and the descent of Algorithm 3 run for block b, creating the
-    leaf of block b as a "tail leaf"; its payload is recomputed from its raw
-    slices after every append.  When the block's last slice arrives, the
+    leaf of block b as a "tail leaf"; its payload is Tucker-ALS of the raw
+    slices received so far.  (It is computed lazily, when the block completes
+    or before the next Recall: only its latest state can be observed, so this
+    equals recomputing it after every append.)  When the block's last slice arrives, the
     descent of Algorithm 3 runs again and performs the deferred Stitch steps
     (a node v becomes intermediate when tau_v = b + 1).  With B = 1 both
     descents happen in the same append, which is Algorithm 3/4 verbatim.
@@ -58,6 +60,7 @@ class StreamSegmentTree:
         self.T = 0                 # timespan in slices
         self.root = None
         self.tail = []             # raw slices of the open block
+        self.tail_dirty = False    # tail leaf payload older than its raw slices
         self.stitch_count = 0      # number of Stitch calls made by appends
 
     # ----- helpers -------------------------------------------------------
@@ -112,11 +115,18 @@ class StreamSegmentTree:
             self.tail = []
         self.tail.append(X_T)
         self.T += 1
-        leaf = self._find_leaf(b)
-        leaf.H, leaf.V = self._leaf_payload(np.stack(self.tail, axis=0))
+        self.tail_dirty = True
         if off == self.B - 1:
+            self._refresh_tail()
             self._insert(self.root, b, complete=True)
             self.tail = []
+
+    def _refresh_tail(self):
+        """Decompose the open (tail) leaf from its raw slices, if stale."""
+        if self.tail_dirty and self.tail:
+            leaf = self._find_leaf((self.T - 1) // self.B)
+            leaf.H, leaf.V = self._leaf_payload(np.stack(self.tail, axis=0))
+        self.tail_dirty = False
 
     def build(self, X):
         """T successive appends (the definition of building the tree over X)."""
@@ -134,6 +144,7 @@ class StreamSegmentTree:
     def recall(self, ts, te, v=None):
         """Pruned hit set of [ts, te) as a time-ordered list of nodes."""
         if v is None:
+            self._refresh_tail()
             v = self.root
         lo, hi = self.slice_range(v)
         ov = max(0, min(te, hi) - max(ts, lo))
