@@ -154,6 +154,40 @@ int64_t tk_launch_count(const tk_tree* t);
 
 const char* tk_strerror(int code);
 
+/* ---- Allocation-free range queries (no counterpart in the paper) --------
+ *
+ * tk_range_query_batch_noalloc answers the same batched range queries as
+ * tk_range_query_batch with io = TK_IO_DEVICE, bit for bit, but makes no
+ * device allocation of any kind: no cudaMalloc/cudaFree and no allocating
+ * library routine.  It exists for callers that cannot let a library allocate
+ * device memory at query time: code that runs under a memory manager or
+ * arena of its own (an embedding runtime, a database engine), real-time or
+ * serving loops whose latency budget rules out the device-wide
+ * synchronization that cudaMalloc/cudaFree may cause, and processes that
+ * must keep a fixed device-memory footprint after start-up.
+ *
+ * Its scratch is one file-scope device array of TK_NOALLOC_SCRATCH_BYTES
+ * (16 MiB), held by every GPU that loads the library until the process
+ * exits.  The first call on a device resolves the array's address on that
+ * device (set-up, once per device); make that first call before any CUDA
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents: the call clears what must start at zero (its status word), and
+ * calls whose work overlaps on the GPU (two streams, two trees, two host
+ * threads) race on it, so serialize them.
+ *
+ * ranges (2n int64), offsets (n+1 int64, from tk_batch_layout) and out are
+ * device pointers owned by the caller, as for tk_range_query_batch.  info is
+ * an optional host array of n reports; with info the call synchronizes and
+ * also reports device-side errors, without it the call is asynchronous.
+ * Returns TK_ERR_TOO_BIG when one query's workspace (which grows with the
+ * tree's capacity, ranks and dimensions) does not fit the scratch array,
+ * TK_ERR_STATE when the open leaf block still awaits its decomposition (any
+ * regular query, tk_node_payload, or the append that completes the block
+ * decomposes it), and the usual argument and rank errors. */
+#define TK_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ranges_dev, const int64_t* offsets_dev,
+                                 const int32_t* ranks, void* out_dev, tk_query_info* info);
+
 #ifdef __cplusplus
 }
 #endif

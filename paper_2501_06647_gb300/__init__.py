@@ -67,6 +67,9 @@ _SIGS = {
     "tk_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "tk_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "tk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "tk_range_query_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p]),
 }
 
 _lib_handle = None
@@ -250,6 +253,17 @@ class Tree:
         ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
         _check(lib().tk_range_query_batch(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), ip,
                                           TK_IO_DEVICE), "tk_range_query_batch")
+
+    def query_batch_noalloc(self, ranges, offsets, out, ranks=None, info=None):
+        """Batched range queries that make no device allocation (device buffers).
+
+        Same results as query_batch; the engine's scratch is a fixed 16 MiB
+        device array shared by all such calls (serialize overlapping calls).
+        """
+        rarr, _ = self._ranks_arg(ranks)
+        ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
+        _check(lib().tk_range_query_batch_noalloc(self.h, int(ranges.shape[0]), _ptr(ranges), _ptr(offsets),
+                                                  rarr, _ptr(out), ip), "tk_range_query_batch_noalloc")
 
     def query_batch_host(self, ranges, offsets=None, out=None, ranks=None, with_info=True):
         """Batched range queries through the C ABI with HOST buffers (copies inside the call)."""

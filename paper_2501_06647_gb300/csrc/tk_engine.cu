@@ -778,3 +778,83 @@ int tk_node_payload(tk_tree* t, int level, int64_t index, void* out_host, int64_
 }
 
 }  // extern "C"
+
+// ---- Allocation-free batched range queries ---------------------------------
+// The scratch of tk_range_query_batch_noalloc: a fixed device array instead of
+// the tree's allocated workspaces.  Layout per call: [0, 256) status word,
+// then the optional per-query reports, then one workspace chunk per CTA.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TK_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+struct NoAllocDevice {
+  std::once_flag once;
+  void* ptr = nullptr;   // device address of g_noalloc_scratch on this device
+  int rc = TK_ERR_CUDA;
+};
+NoAllocDevice g_noalloc_dev[kMaxDevices];
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ranges_dev,
+                                            const int64_t* offsets_dev, const int32_t* ranks, void* out_dev,
+                                            tk_query_info* info) {
+  if (!t || n < 1 || !ranges_dev || !offsets_dev || !out_dev) return TK_ERR_ARG;
+  if (t->dev < 0 || t->dev >= kMaxDevices) return TK_ERR_ARG;
+  int rq[TK_MAXP];
+  int rc = check_ranks(t, ranks, rq);
+  if (rc) return rc;
+  // the open block would need the leaf kernel (and its workspace) first
+  if (t->tail_dirty && t->T > t->nb * t->cfg.leaf_slices) return TK_ERR_STATE;
+  DeviceGuard g(t->dev);
+  // set-up, once per device, with the tree's device current
+  NoAllocDevice& d = g_noalloc_dev[t->dev];
+  std::call_once(d.once, [&d] {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    d.ptr = p;
+    d.rc = (e == cudaSuccess && p != nullptr) ? TK_OK : TK_ERR_CUDA;
+  });
+  if (d.rc != TK_OK) return d.rc;
+  // size check: one query's workspace must fit next to the status word and reports
+  if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
+  const int64_t per_cta = stitch_ws_bound(t, max_hits(t, t->nbcap));
+  const size_t per_cta_bytes = round256((size_t)per_cta * t->es);
+  const size_t info_bytes = info ? round256(sizeof(tk_query_info) * (size_t)n) : 0;
+  const size_t head = 256 + info_bytes;
+  if (head + per_cta_bytes > TK_NOALLOC_SCRATCH_BYTES) return TK_ERR_TOO_BIG;
+  if (t->T == 0) return TK_ERR_RANGE;
+  const int fit = (int)std::min<size_t>((TK_NOALLOC_SCRATCH_BYTES - head) / per_cta_bytes, 1 << 20);
+  const int grid = std::max(1, std::min(grid_for(t, false, n), fit));
+  char* base = (char*)d.ptr;
+  rc = cuda_ok(cudaMemsetAsync(base, 0, 256, t->stream));  // status word starts at zero
+  if (rc) return rc;
+  TkWorkspace ws{};
+  ws.base = base + head;
+  ws.per_cta = (int64_t)(per_cta_bytes / t->es);
+  ws.nsm = t->nsm_stitch;
+  ws.status = (int*)base;
+  TkQueryBatch qb{};
+  qb.n = n;
+  qb.ranges = ranges_dev;
+  qb.offsets = offsets_dev;
+  qb.out = out_dev;
+  qb.info = info ? (tk_query_info*)(base + 256) : nullptr;
+  for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
+  rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws, grid, t->stream);
+  t->launches += 1;
+  if (rc) return rc;
+  if (!info) return TK_OK;
+  int st = 0;
+  rc = cuda_ok(cudaMemcpyAsync(info, base + 256, sizeof(tk_query_info) * (size_t)n, cudaMemcpyDeviceToHost,
+                               t->stream));
+  if (rc == TK_OK) rc = cuda_ok(cudaMemcpyAsync(&st, base, sizeof(int), cudaMemcpyDeviceToHost, t->stream));
+  if (rc == TK_OK) rc = cuda_ok(cudaStreamSynchronize(t->stream));
+  if (rc) return rc;
+  if (st == TK_DEV_ERR_RANGE) return TK_ERR_RANGE;
+  if (st != 0) return TK_ERR_WORKSPACE;
+  return TK_OK;
+}
