@@ -81,6 +81,9 @@ typedef struct tk_query_info {
   int32_t iters;                    /* ALS iterations run; < 0 on a device-side error */
   int32_t n_hits;                   /* hit-set size s */
   double fit_err;                   /* sqrt(1 - ||G||^2 / ||Y~||^2) of the stitched tensor */
+  int32_t eig_sweeps;               /* Jacobi sweeps summed over the query's eigenproblems */
+  int32_t eig_max_order;            /* largest eigenproblem order of the query */
+  int64_t device_cycles;            /* SM clock cycles the query's warp spent on it */
 } tk_query_info;
 
 typedef struct tk_tree tk_tree;

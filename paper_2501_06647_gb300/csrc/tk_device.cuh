@@ -1,7 +1,9 @@
-// Block-cooperative building blocks for the small dense linear algebra of a
-// stitch or leaf job.  Every routine is called by all threads of the CTA,
-// works on plain pointers (shared or global memory), uses a fixed reduction
-// order (so repeated runs are bit-identical) and ends with __syncthreads().
+// Cooperative building blocks for the small dense linear algebra of a stitch
+// or leaf job.  Every routine is executed by all threads of a *group* -- one
+// warp (WarpGroup, the stitch kernel: one query per warp) or one CTA
+// (BlockGroup, the leaf kernel) -- works on plain pointers (shared or global
+// memory), uses a fixed reduction order (so repeated runs are bit-identical)
+// and ends with a group barrier.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,32 +20,48 @@ template <class S> __device__ __forceinline__ S warp_sum(S v) {
   return v;
 }
 
-// Sum of one value per thread; every thread gets the total.  red: >= 33 S.
-template <class S> __device__ S block_sum(S v, S* red) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    S x = lane < nw ? red[lane] : S(0);
-    x = warp_sum(x);
-    if (lane == 0) red[32] = x;
+// One warp.  Warp-synchronous: __syncwarp orders shared and global memory
+// among its lanes.
+struct WarpGroup {
+  static __device__ __forceinline__ int rank() { return threadIdx.x & 31; }
+  static __device__ __forceinline__ int size() { return 32; }
+  static __device__ __forceinline__ int nwarps() { return 1; }
+  static __device__ __forceinline__ void sync() { __syncwarp(); }
+  template <class S> static __device__ __forceinline__ S sum(S v, S*) { return warp_sum(v); }
+};
+
+// One CTA.  sum() needs >= 33 elements of shared scratch.
+struct BlockGroup {
+  static __device__ __forceinline__ int rank() { return threadIdx.x; }
+  static __device__ __forceinline__ int size() { return blockDim.x; }
+  static __device__ __forceinline__ int nwarps() { return blockDim.x >> 5; }
+  static __device__ __forceinline__ void sync() { __syncthreads(); }
+  template <class S> static __device__ S sum(S v, S* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      S x = lane < nw ? red[lane] : S(0);
+      x = warp_sum(x);
+      if (lane == 0) red[32] = x;
+    }
+    __syncthreads();
+    const S r = red[32];
+    __syncthreads();
+    return r;
   }
-  __syncthreads();
-  S r = red[32];
-  __syncthreads();
-  return r;
-}
+};
 
-template <class S> __device__ S sum_squares(const S* x, int64_t n, S* red) {
+template <class G, class S> __device__ S sum_squares(const S* x, int64_t n, S* red) {
   S a = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += x[i] * x[i];
-  return block_sum(a, red);
+  for (int64_t i = G::rank(); i < n; i += G::size()) a += x[i] * x[i];
+  return G::template sum<S>(a, red);
 }
 
-__device__ __forceinline__ int64_t prod_range(const int* d, int a, int b) {
-  int64_t p = 1;
+__device__ __forceinline__ int prod_range(const int* d, int a, int b) {
+  int p = 1;
   for (int m = a; m < b; ++m) p *= d[m];
   return p;
 }
@@ -51,63 +69,128 @@ __device__ __forceinline__ int64_t prod_range(const int* d, int a, int b) {
 // Mode-n product of a C-order tensor X (dims d[0..p-1]) with a matrix M of
 // shape a x d[n], M(alpha, j) = M[alpha*mrs + j*mcs]:
 //   Y[o, alpha, i] = sum_j M(alpha, j) X[o, j, i]   (Appendix A: mat_n(Y) = M mat_n(X)).
-// Y has dims d with d[n] replaced by a.  accumulate: Y += result.
-template <class S>
-__device__ void ttm(const S* X, const int* d, int p, int n, const S* M, int64_t mrs, int64_t mcs,
-                    int a, S* Y, bool accumulate) {
-  const int64_t outer = prod_range(d, 0, n), inner = prod_range(d, n + 1, p);
-  const int dn = d[n];
-  const int64_t total = outer * a * inner;
-  for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int64_t i = idx % inner;
-    const int64_t t = idx / inner;
-    const int al = (int)(t % a);
-    const int64_t o = t / a;
-    const S* xp = X + o * dn * inner + i;
-    const S* mp = M + al * mrs;
-    S acc = 0;
-    for (int j = 0; j < dn; ++j) acc += mp[j * mcs] * xp[j * inner];
-    if (accumulate) Y[idx] += acc; else Y[idx] = acc;
-  }
-  __syncthreads();
-}
-
-// Mode-n Gram mat_n(X) mat_n(X)^T (d[n] x d[n], leading dimension lda).
-template <class S>
-__device__ void mode_gram(const S* X, const int* d, int p, int n, S* A, int lda, bool accumulate) {
-  const int64_t outer = prod_range(d, 0, n), inner = prod_range(d, n + 1, p);
-  const int dn = d[n];
-  for (int idx = threadIdx.x; idx < dn * dn; idx += blockDim.x) {
-    const int a = idx / dn, b = idx % dn;
-    if (a > b) continue;
-    S acc = 0;
-    for (int64_t o = 0; o < outer; ++o) {
-      const S* pa = X + (o * dn + a) * inner;
-      const S* pb = X + (o * dn + b) * inner;
-      for (int64_t i = 0; i < inner; ++i) acc += pa[i] * pb[i];
-    }
-    if (accumulate) {
-      A[a * lda + b] += acc;
-      if (a != b) A[b * lda + a] += acc;
+// Y has dims d with d[n] replaced by a.  accumulate: Y += result.  Each
+// thread computes 4 consecutive alpha for one (o, i), so every X element it
+// loads feeds 4 FMAs; consecutive threads take consecutive i (coalesced).
+template <class G, class S>
+__device__ void ttm(const S* X, const int* d, int p, int n, const S* M, int mrs, int mcs, int a, S* Y,
+                    bool accumulate) {
+  constexpr int CH = 4;
+  const int outer = prod_range(d, 0, n), inner = prod_range(d, n + 1, p), dn = d[n];
+  const int pairs = outer * inner;
+  const int nch = (a + CH - 1) / CH;
+  const int total = pairs * nch;
+  // element t = ch * pairs + o * inner + i, walked with a stride of G::size()
+  // by carries instead of per-element division
+  const int nt = G::size();
+  const int dch = nt / pairs, dpi = nt - dch * pairs, dout = dpi / inner, din = dpi - dout * inner;
+  int t = G::rank();
+  int ch = t / pairs, o = (t - ch * pairs) / inner, i = t - ch * pairs - o * inner;
+  for (; t < total; t += nt) {
+    const int a0 = ch * CH;
+    const S* xp = X + (o * dn) * inner + i;
+    const S* mp = M + a0 * mrs;
+    S acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = 0;
+    if (a0 + CH <= a) {
+      for (int j = 0; j < dn; ++j) {
+        const S x = xp[j * inner];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) acc[c] += mp[c * mrs + j * mcs] * x;
+      }
     } else {
-      A[a * lda + b] = acc;
-      A[b * lda + a] = acc;
+      for (int j = 0; j < dn; ++j) {
+        const S x = xp[j * inner];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (a0 + c < a) acc[c] += mp[c * mrs + j * mcs] * x;
+      }
+    }
+    S* yp = Y + (o * a + a0) * inner + i;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      if (a0 + c < a) {
+        if (accumulate) yp[c * inner] += acc[c];
+        else yp[c * inner] = acc[c];
+      }
+    }
+    i += din;
+    o += dout;
+    ch += dch;
+    if (i >= inner) {
+      i -= inner;
+      ++o;
+    }
+    if (o >= outer) {
+      o -= outer;
+      ++ch;
     }
   }
-  __syncthreads();
+  G::sync();
 }
 
-// C (M x N) = A (M x K) * B (K x N) with general strides; beta = 0 or 1.
-template <class S>
-__device__ void gemm(int M, int N, int K, const S* A, int64_t ars, int64_t acs, const S* B,
-                     int64_t brs, int64_t bcs, S* C, int64_t crs, int64_t ccs, bool accumulate) {
-  for (int64_t idx = threadIdx.x; idx < (int64_t)M * N; idx += blockDim.x) {
-    const int i = (int)(idx / N), j = (int)(idx % N);
+// Mode-n Gram mat_n(X) mat_n(X)^T (d[n] x d[n], leading dimension lda); each
+// thread takes one (a, b) with a <= b of the packed upper triangle.
+template <class G, class S>
+__device__ void mode_gram(const S* X, const int* d, int p, int n, S* A, int lda, bool accumulate) {
+  const int outer = prod_range(d, 0, n), inner = prod_range(d, n + 1, p), dn = d[n];
+  const int npairs = dn * (dn + 1) / 2;
+  const int nt = G::size();
+  int idx = G::rank();
+  if (idx < npairs) {  // no early return: every thread must reach the one barrier below
+    // row a of the packed upper triangle: idx in [a(2dn-a+1)/2, (a+1)(2dn-a)/2)
+    int a = (int)((2.f * dn + 1.f - sqrtf((2.f * dn + 1.f) * (2.f * dn + 1.f) - 8.f * idx)) * 0.5f);
+    if (a < 0) a = 0;
+    while (a > 0 && a * (2 * dn - a + 1) / 2 > idx) --a;
+    while ((a + 1) * (2 * dn - a) / 2 <= idx) ++a;
+    int b = idx - a * (2 * dn - a + 1) / 2 + a;
+    for (; idx < npairs; idx += nt) {
+      S acc = 0;
+      for (int o = 0; o < outer; ++o) {
+        const S* pa = X + (o * dn + a) * inner;
+        const S* pb = X + (o * dn + b) * inner;
+        for (int i = 0; i < inner; ++i) acc += pa[i] * pb[i];
+      }
+      if (accumulate) {
+        A[a * lda + b] += acc;
+        if (a != b) A[b * lda + a] += acc;
+      } else {
+        A[a * lda + b] = acc;
+        A[b * lda + a] = acc;
+      }
+      // advance nt positions along the packed rows (row a holds columns a..dn-1)
+      b += nt;
+      while (b >= dn && a < dn - 1) {
+        b -= dn - (a + 1);
+        ++a;
+      }
+    }
+  }
+  G::sync();
+}
+
+// C (M x N) = A (M x K) * B (K x N) with general strides; accumulate: C +=.
+template <class G, class S>
+__device__ void gemm(int M, int N, int K, const S* A, int ars, int acs, const S* B, int brs, int bcs, S* C,
+                     int64_t crs, int ccs, bool accumulate) {
+  const int nt = G::size();
+  const int di = nt / N, dj = nt - di * N;
+  int idx = G::rank();
+  int i = idx / N, j = idx - (idx / N) * N;
+  for (; idx < M * N; idx += nt) {
     S acc = 0;
     for (int k = 0; k < K; ++k) acc += A[i * ars + k * acs] * B[k * brs + j * bcs];
-    if (accumulate) C[i * crs + j * ccs] += acc; else C[i * crs + j * ccs] = acc;
+    if (accumulate) C[i * crs + j * ccs] += acc;
+    else C[i * crs + j * ccs] = acc;
+    j += dj;
+    i += di;
+    if (j >= N) {
+      j -= N;
+      ++i;
+    }
   }
-  __syncthreads();
+  G::sync();
 }
 
 // Householder QR of the row-major m x n matrix A (leading dimension lda), in
@@ -115,11 +198,11 @@ __device__ void gemm(int M, int N, int K, const S* A, int64_t ars, int64_t acs, 
 // on return the upper triangle holds R (min(m,n) x n) and the part below the
 // diagonal holds the reflector vectors v_j (v_j[j] = 1 implicit), with
 // H_j = I - tau_j v_j v_j^T and A_in = H_0 H_1 ... H_{k-1} R.  tau: min(m,n).
-// sc: >= 3 S of shared scratch.
-template <class S>
-__device__ void householder_qr(S* A, int m, int n, int64_t lda, S* tau, S* sc) {
+// sc: >= 3 S of group-private shared scratch.
+template <class G, class S>
+__device__ void householder_qr(S* A, int m, int n, int lda, S* tau, S* sc) {
   const int kmax = m < n ? m : n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = G::rank() & 31, warp = G::rank() >> 5, nw = G::nwarps();
   for (int j = 0; j < kmax; ++j) {
     if (warp == 0) {
       S s = 0;
@@ -143,11 +226,11 @@ __device__ void householder_qr(S* A, int m, int n, int64_t lda, S* tau, S* sc) {
         tau[j] = t;
       }
     }
-    __syncthreads();
+    G::sync();
     const S t = sc[0], scale = sc[1], beta = sc[2];
     if (t != S(0)) {
-      for (int i = j + 1 + (int)threadIdx.x; i < m; i += blockDim.x) A[i * lda + j] *= scale;
-      __syncthreads();
+      for (int i = j + 1 + G::rank(); i < m; i += G::size()) A[i * lda + j] *= scale;
+      G::sync();
       for (int k = j + 1 + warp; k < n; k += nw) {
         S w = 0;
         for (int i = j + 1 + lane; i < m; i += 32) w += A[i * lda + j] * A[i * lda + k];
@@ -158,19 +241,19 @@ __device__ void householder_qr(S* A, int m, int n, int64_t lda, S* tau, S* sc) {
         for (int i = j + 1 + lane; i < m; i += 32) A[i * lda + k] -= w * A[i * lda + j];
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) A[j * lda + j] = beta;
-    __syncthreads();
+    G::sync();
+    if (G::rank() == 0) A[j * lda + j] = beta;
+    G::sync();
   }
 }
 
 // Y (m x ncols, leading dimension ldy) <- H_0 H_1 ... H_{k-1} Y, the Q factor
 // of householder_qr applied to Y.  To form Q [E; 0], fill Y with E on its
 // first rows and zeros below before the call.
-template <class S>
-__device__ void householder_apply_q(const S* A, int m, int kmax, int64_t lda, const S* tau, S* Y,
-                                    int ncols, int64_t ldy) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+template <class G, class S>
+__device__ void householder_apply_q(const S* A, int m, int kmax, int lda, const S* tau, S* Y, int ncols,
+                                    int64_t ldy) {
+  const int lane = G::rank() & 31, warp = G::rank() >> 5, nw = G::nwarps();
   for (int j = kmax - 1; j >= 0; --j) {
     const S t = tau[j];
     if (t == S(0)) continue;
@@ -183,48 +266,79 @@ __device__ void householder_apply_q(const S* A, int m, int kmax, int64_t lda, co
       if (lane == 0) Y[j * ldy + c] -= w;
       for (int i = j + 1 + lane; i < m; i += 32) Y[i * ldy + c] -= w * A[i * lda + j];
     }
-    __syncthreads();
+    G::sync();
   }
 }
 
-// Shared scratch of jacobi_eig for order n: pairs of the round-robin schedule.
-struct JacobiScratch {
-  int* pq;    // >= n/2+1
+// Scratch of jacobi_eig for order n: the round-robin schedule and rotations.
+template <class S> struct JacobiScratch {
+  int* pq;    // >= n/2 + 1
+  S* c;       // >= n/2 + 1
+  S* s;       // >= n/2 + 1
   int* flag;  // 1
+  S* red;     // group reduction scratch
+  int* nsw;   // 1: sweeps of the last call
 };
 
-// Symmetric eigendecomposition of the n x n matrix A (leading dimension lda)
+// Symmetric eigendecomposition of the n x n matrix A (leading dimension n)
 // by the cyclic two-sided Jacobi method with the round-robin parallel
 // ordering (Golub & Van Loan, Sections 8.5.2-8.5.5: every round applies n/2
-// disjoint rotations J(p,q) with the Rutishauser formula of Algorithm 8.5.1,
-// A <- J^T A J, V <- V J).  A is destroyed (its diagonal ends as the
-// eigenvalues, copied to w); V (ldv) receives the eigenvectors as columns.
+// disjoint rotations J(p,q) given by the Rutishauser formula of Algorithm
+// 8.5.1, A <- J^T A J, V <- V J).
+//
+// warm: V already holds an orthogonal matrix (the eigenvectors of a nearby
+// matrix, e.g. the previous ALS iteration's); A is first replaced by V^T A V
+// (through T, n x n scratch) and the sweeps then start from a nearly diagonal
+// matrix.  Otherwise V starts as the identity.  Either way, on return V holds
+// orthonormal eigenvectors of the input A as columns and w the eigenvalues.
 // A rotation is skipped when |a_pq| <= eps sqrt(|a_pp a_qq|) or
-// |a_pq| <= 1e-3 eps ||A||_F; the sweep loop stops when a whole sweep skips
-// every rotation or after max_sweeps.  Returns the number of sweeps run.
-template <class S>
-__device__ int jacobi_eig(int n, S* A, int64_t lda, S* V, int64_t ldv, S* w, S* cs, JacobiScratch js,
-                          S* red, int max_sweeps) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int i = idx / n, j = idx % n;
-    V[i * ldv + j] = (i == j) ? S(1) : S(0);
+// |a_pq| <= eps ||A||_F (an entry at the rounding level of A moves no
+// eigenvector by more than rounding); the sweeps stop after one in which
+// every rotation was skipped, or after max_sweeps.
+//
+// jacobi_prepare does the warm transform (or V = I) and returns the absolute
+// skip floor; jacobi_sweeps runs the sweeps.  Both are executed by group G.
+template <class G, class S>
+__device__ S jacobi_prepare(int n, S* A, S* V, S* T, bool warm, JacobiScratch<S> js) {
+  const int tid = G::rank(), nt = G::size();
+  const int nn = n * n;
+  if (warm) {
+    for (int idx = tid; idx < nn; idx += nt) {  // T = A V
+      const int i = idx / n, j = idx % n;
+      S acc = 0;
+      for (int k = 0; k < n; ++k) acc += A[i * n + k] * V[k * n + j];
+      T[idx] = acc;
+    }
+    G::sync();
+    for (int idx = tid; idx < nn; idx += nt) {  // A = V^T T, symmetrized
+      const int i = idx / n, j = idx % n;
+      if (i > j) continue;
+      S acc = 0;
+      for (int k = 0; k < n; ++k) acc += V[k * n + i] * T[k * n + j];
+      A[i * n + j] = acc;
+      A[j * n + i] = acc;
+    }
+  } else {
+    for (int idx = tid; idx < nn; idx += nt) V[idx] = ((idx / n) == (idx % n)) ? S(1) : S(0);
   }
+  G::sync();
   S a2 = 0;
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const S v = A[(idx / n) * lda + (idx % n)];
-    a2 += v * v;
-  }
-  const S normA = sqrt(block_sum(a2, red));
+  for (int idx = tid; idx < nn; idx += nt) a2 += A[idx] * A[idx];
+  return Eps<S>::v() * sqrt(G::template sum<S>(a2, js.red));
+}
+
+template <class G, class S>
+__device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch<S> js, int max_sweeps) {
+  const int tid = G::rank(), nt = G::size();
   const S eps = Eps<S>::v();
-  const S floor_abs = S(1e-3) * eps * normA;
   const int m = n + (n & 1), half = m / 2;
-  S* cc = cs;
-  S* ss = cs + half + 1;
+  // (pair k, column j) of element idx = k n + j, walked by carries
+  const int dk = nt / (n > 0 ? n : 1), dj = nt - dk * n;
+  const int k0 = tid / (n > 0 ? n : 1), j0 = tid - k0 * n;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *js.flag = 0;
-    __syncthreads();
+    G::sync();
     for (int rd = 0; rd < m - 1; ++rd) {
       for (int k = tid; k < half; k += nt) {
         int a, b;
@@ -232,15 +346,17 @@ __device__ int jacobi_eig(int n, S* A, int64_t lda, S* V, int64_t ldv, S* w, S* 
           a = rd;
           b = m - 1;
         } else {
-          a = (rd + k) % (m - 1);
-          b = (rd - k + m - 1) % (m - 1);
+          a = rd + k;
+          if (a >= m - 1) a -= m - 1;
+          b = rd - k;
+          if (b < 0) b += m - 1;
         }
         const int pp = a < b ? a : b, qq = a < b ? b : a;
         int code = -1;
         S c = 1, s = 0;
         if (qq < n) {
-          const S apq = A[pp * lda + qq];
-          const S app = A[pp * lda + pp], aqq = A[qq * lda + qq];
+          const S apq = A[pp * n + qq];
+          const S app = A[pp * n + pp], aqq = A[qq * n + qq];
           const S aapq = fabs(apq);
           if (aapq > floor_abs && aapq > eps * sqrt(fabs(app * aqq))) {
             const S theta = (aqq - app) / (S(2) * apq);
@@ -254,53 +370,83 @@ __device__ int jacobi_eig(int n, S* A, int64_t lda, S* V, int64_t ldv, S* w, S* 
           }
         }
         js.pq[k] = code;
-        cc[k] = c;
-        ss[k] = s;
+        js.c[k] = c;
+        js.s[k] = s;
       }
-      __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {
-        const int k = idx / n, j = idx % n;
+      G::sync();
+      for (int idx = tid, k = k0, j = j0; idx < half * n; idx += nt) {
         const int code = js.pq[k];
+        if (code >= 0) {
+          const int pp = code & 0xffff, qq = code >> 16;
+          const S c = js.c[k], s = js.s[k];
+          const S apj = A[pp * n + j], aqj = A[qq * n + j];
+          A[pp * n + j] = c * apj - s * aqj;
+          A[qq * n + j] = s * apj + c * aqj;
+        }
+        j += dj;
+        k += dk;
+        if (j >= n) {
+          j -= n;
+          ++k;
+        }
+      }
+      G::sync();
+      for (int idx = tid, k = k0, i = j0; idx < half * n; idx += nt) {
+        const int kk = k, ii = i;
+        i += dj;
+        k += dk;
+        if (i >= n) {
+          i -= n;
+          ++k;
+        }
+        const int code = js.pq[kk];
         if (code < 0) continue;
         const int pp = code & 0xffff, qq = code >> 16;
-        const S c = cc[k], s = ss[k];
-        const S apj = A[pp * lda + j], aqj = A[qq * lda + j];
-        A[pp * lda + j] = c * apj - s * aqj;
-        A[qq * lda + j] = s * apj + c * aqj;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {
-        const int k = idx / n, i = idx % n;
-        const int code = js.pq[k];
-        if (code < 0) continue;
-        const int pp = code & 0xffff, qq = code >> 16;
-        const S c = cc[k], s = ss[k];
-        const S aip = A[i * lda + pp], aiq = A[i * lda + qq];
+        const S c = js.c[kk], s = js.s[kk];
+        const S aip = A[ii * n + pp], aiq = A[ii * n + qq];
         S nip = c * aip - s * aiq, niq = s * aip + c * aiq;
-        if (i == pp) niq = 0;
-        if (i == qq) nip = 0;
-        A[i * lda + pp] = nip;
-        A[i * lda + qq] = niq;
-        const S vip = V[i * ldv + pp], viq = V[i * ldv + qq];
-        V[i * ldv + pp] = c * vip - s * viq;
-        V[i * ldv + qq] = s * vip + c * viq;
+        if (ii == pp) niq = 0;
+        if (ii == qq) nip = 0;
+        A[ii * n + pp] = nip;
+        A[ii * n + qq] = niq;
+        const S vip = V[ii * n + pp], viq = V[ii * n + qq];
+        V[ii * n + pp] = c * vip - s * viq;
+        V[ii * n + qq] = s * vip + c * viq;
       }
-      __syncthreads();
+      G::sync();
     }
     const int any = *js.flag;
-    __syncthreads();
+    G::sync();
     if (!any) break;
   }
-  for (int i = tid; i < n; i += nt) w[i] = A[i * lda + i];
-  __syncthreads();
+  for (int i = tid; i < n; i += nt) w[i] = A[i * n + i];
+  G::sync();
   return sweep;
 }
 
-// E (n x r, leading dimension lde) <- the eigenvectors (columns of V) of the
-// r largest eigenvalues w, in descending order (ties by index).
-template <class S>
-__device__ void select_top(int n, const S* w, const S* V, int64_t ldv, int r, S* E, int64_t lde) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+// The whole eigendecomposition by group G.  Orders up to 32 run their sweeps
+// on the group's first warp alone (warp-synchronous rounds, no block-wide
+// barrier per round); larger orders use every thread of G.  Returns the
+// sweeps run.
+template <class G, class S>
+__device__ int jacobi_eig(int n, S* A, S* V, S* T, bool warm, S* w, JacobiScratch<S> js, int max_sweeps) {
+  const S floor_abs = jacobi_prepare<G, S>(n, A, V, T, warm, js);
+  if (G::size() > 32 && n <= 32) {
+    if ((G::rank() >> 5) == 0) {
+      const int sw = jacobi_sweeps<WarpGroup, S>(n, A, V, floor_abs, w, js, max_sweeps);
+      if (G::rank() == 0) *js.nsw = sw;
+    }
+    G::sync();
+    return *js.nsw;
+  }
+  return jacobi_sweeps<G, S>(n, A, V, floor_abs, w, js, max_sweeps);
+}
+
+// E (n x r, leading dimension lde) <- the eigenvectors (columns of V, n x n)
+// of the r largest eigenvalues w, in descending order (ties by index).
+template <class G, class S>
+__device__ void select_top(int n, const S* w, const S* V, int r, S* E, int lde) {
+  for (int i = G::rank(); i < n; i += G::size()) {
     const S wi = w[i];
     int rank = 0;
     for (int j = 0; j < n; ++j) {
@@ -308,9 +454,9 @@ __device__ void select_top(int n, const S* w, const S* V, int64_t ldv, int r, S*
       if (wj > wi || (wj == wi && j < i)) ++rank;
     }
     if (rank < r)
-      for (int row = 0; row < n; ++row) E[row * lde + rank] = V[row * ldv + i];
+      for (int row = 0; row < n; ++row) E[row * lde + rank] = V[row * n + i];
   }
-  __syncthreads();
+  G::sync();
 }
 
 }  // namespace tk

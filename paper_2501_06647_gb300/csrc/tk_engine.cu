@@ -229,7 +229,7 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   int64_t rprod = 1;
   for (int n = 0; n < p; ++n) rprod *= r[n];
   const int64_t Tcap = t->nbcap * t->cfg.leaf_slices;
-  int64_t tot = 0;
+  int64_t tot = ((int64_t)TK_MAXH * TK_HITREC_BYTES + (int64_t)t->es - 1) / (int64_t)t->es;
   tot += hmax * round32(rprod);
   tot += 2 * (round32(Tcap * r[0]) + round32(r[0]));  // at most two partial hits
   int64_t k[TK_MAXP], c[TK_MAXP];
@@ -239,10 +239,10 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
     const int64_t Dn = t->cfg.dims[n];
     k[n] = (int64_t)hmax * r[n];
     c[n] = std::min<int64_t>(Dn, k[n]);
-    tot += round32(Dn * k[n]) + round32(k[n]) + round32(c[n] * k[n]) + round32(c[n] * r[n]);
+    tot += round32(Dn * k[n]) + round32(k[n]) + round32(c[n] * k[n]) + round32(c[n] * r[n]) + round32(c[n] * c[n]);
     neig = std::max(neig, c[n]);
   }
-  tot += round32(c[0] * r[0]);
+  tot += round32(c[0] * r[0]) + round32(c[0] * c[0]);
   int64_t Kel = k[0];
   for (int m = 1; m < p; ++m) Kel *= r[m];
   tot += round32(Kel);
@@ -257,8 +257,8 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   for (int m = 0; m < p; ++m) wmax = std::max<int64_t>(wmax, (int64_t)r[m] * r[m]);
   tot += round32(wmax);
   tot += round32(rprod);
-  // eig scratch if it spills out of shared memory
-  tot += 2 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
+  // T of the warm start, and the eig scratch if it spills out of shared memory
+  tot += 3 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
   return tot + 256;
 }
 
@@ -266,15 +266,15 @@ int64_t leaf_ws_bound(const tk_tree* t) {
   const int p = t->p;
   const int B = t->cfg.leaf_slices;
   int64_t tot = 0, xel = B, neig = B, gel = 1;
-  tot += round32((int64_t)B * t->cfg.ranks[0]);
+  tot += round32((int64_t)B * t->cfg.ranks[0]) + round32((int64_t)B * B);
   for (int n = 1; n < p; ++n) {
-    tot += round32(t->cfg.dims[n] * t->cfg.ranks[n]);
+    tot += round32(t->cfg.dims[n] * t->cfg.ranks[n]) + round32(t->cfg.dims[n] * t->cfg.dims[n]);
     xel *= t->cfg.dims[n];
     neig = std::max<int64_t>(neig, t->cfg.dims[n]);
   }
   for (int n = 0; n < p; ++n) gel *= t->cfg.ranks[n];
   tot += 2 * round32(xel) + round32(gel);
-  tot += 2 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
+  tot += 3 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
   return tot + 256;
 }
 
@@ -284,13 +284,15 @@ int max_hits(const tk_tree* t, int64_t nbt) {
 }
 
 // Largest eig order kept in shared memory for each kernel family.
+// One CTA of stitch_warps() warps runs one stitch job at a time; the job
+// places its hottest buffers in a shared arena of this many bytes (four CTAs
+// per SM) and the rest in its global workspace chunk.
 int pick_nsm_stitch(const tk_tree* t) {
-  const int hmax = max_hits(t, std::max<int64_t>(nbt_of(t), t->nbcap));
-  int need = hmax * t->cfg.ranks[0];
-  for (int n = 1; n < t->p; ++n) need = std::max<int>(need, (int)std::min<int64_t>(t->cfg.dims[n], (int64_t)hmax * t->cfg.ranks[n]));
-  const int cap = t->es == 8 ? 64 : 96;
-  return std::max(2, std::min(need, cap));
+  (void)t;
+  return 44 * 1024;
 }
+
+int stitch_warps(const tk_tree* t) { (void)t; return 4; }
 
 int pick_nsm_leaf(const tk_tree* t) {
   int need = t->cfg.leaf_slices;
@@ -299,6 +301,7 @@ int pick_nsm_leaf(const tk_tree* t) {
   return std::max(2, std::min(need, cap));
 }
 
+// Stitch workspace: one chunk per CTA of the grid.
 int ensure_ws_stitch(tk_tree* t, int want_ctas) {
   const int hmax = max_hits(t, t->nbcap);
   const int64_t per = stitch_ws_bound(t, hmax);
@@ -332,17 +335,25 @@ TkWorkspace ws_view(const tk_tree* t, bool leaf) {
   TkWorkspace w{};
   w.base = leaf ? t->ws_leaf.ptr : t->ws_stitch.ptr;
   w.per_cta = leaf ? t->ws_leaf_per_cta : t->ws_stitch_per_cta;
-  w.nsm = leaf ? t->nsm_leaf : t->nsm_stitch;
+  w.nsm = leaf ? t->nsm_leaf : 0;
+  w.smem_arena = leaf ? 0 : (size_t)t->nsm_stitch;
+  w.warps = stitch_warps(t);
   w.status = (int*)t->status.ptr;
+  w.counter = (unsigned*)((char*)t->status.ptr + 16);
   return w;
 }
 
+// Grid of a launch with njobs jobs: persistent (at most the resident CTAs),
+// and no more CTAs than needed (a stitch CTA runs one job per warp at a time).
 int grid_for(tk_tree* t, bool leaf, int njobs) {
   const int dtype = t->cfg.dtype;
-  const size_t smem = leaf ? tk_leaf_smem_bytes(dtype, t->nsm_leaf) : tk_stitch_smem_bytes(dtype, t->nsm_stitch);
-  int occ = tk_occupancy(dtype, leaf ? 0 : 1, smem);
+  const int warps = stitch_warps(t);
+  const size_t smem = leaf ? tk_leaf_smem_bytes(dtype, t->nsm_leaf)
+                           : tk_stitch_smem_bytes(dtype, (size_t)t->nsm_stitch);
+  int occ = tk_occupancy(dtype, leaf ? 0 : 1, smem, leaf ? TK_NT : 32 * warps);
   if (occ < 1) occ = 1;
-  return std::max(1, std::min(njobs, occ * t->sm_count));
+  const int need = njobs;
+  return std::max(1, std::min(need, occ * t->sm_count));
 }
 
 // Decompose leaf blocks [first, first+njobs) read from raw (block stride in
@@ -827,6 +838,7 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
   const size_t head = 256 + info_bytes;
   if (head + per_cta_bytes > TK_NOALLOC_SCRATCH_BYTES) return TK_ERR_TOO_BIG;
   if (t->T == 0) return TK_ERR_RANGE;
+  const int warps = stitch_warps(t);
   const int fit = (int)std::min<size_t>((TK_NOALLOC_SCRATCH_BYTES - head) / per_cta_bytes, 1 << 20);
   const int grid = std::max(1, std::min(grid_for(t, false, n), fit));
   char* base = (char*)d.ptr;
@@ -835,8 +847,11 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
   TkWorkspace ws{};
   ws.base = base + head;
   ws.per_cta = (int64_t)(per_cta_bytes / t->es);
-  ws.nsm = t->nsm_stitch;
+  ws.nsm = 0;
+  ws.smem_arena = (size_t)t->nsm_stitch;
+  ws.warps = warps;
   ws.status = (int*)base;
+  ws.counter = (unsigned*)(base + 64);
   TkQueryBatch qb{};
   qb.n = n;
   qb.ranges = ranges_dev;

@@ -8,7 +8,8 @@
 #define TK_MAXP TK_MAX_MODES
 #define TK_MAXL 40      // tree levels (2^39 leaf blocks)
 #define TK_MAXH 64      // hits per stitch job handled by the kernel
-#define TK_NT 256       // threads per CTA of the stitch and leaf kernels
+#define TK_NT 256       // threads per CTA of the leaf kernel; stitch CTAs are <= TK_NT
+#define TK_HITREC_BYTES 160  // bytes of one hit record in a stitch job's workspace
 
 // Device view of a tree: dimensions, the implicit dyadic node numbering and
 // the pooled HBM arena.  Passed by value to every kernel.
@@ -41,10 +42,14 @@ struct TkTreeView {
 };
 
 struct TkWorkspace {
-  void* base;              // per-CTA chunks of `per_cta` elements
+  void* base;              // per-worker chunks of `per_cta` elements (a worker is a
+                           // warp in k_stitch and a CTA in k_leaf)
   int64_t per_cta;
-  int nsm;                 // largest eig order kept in shared memory
+  int nsm;                 // k_leaf: largest eig order kept in shared memory
+  int warps;               // warps per CTA of k_stitch
+  size_t smem_arena;       // k_stitch: bytes of the per-job shared arena
   int* status;             // first device-side error (0 = none)
+  unsigned* counter;       // k_stitch job queue, zeroed before each launch
 };
 
 enum { TK_JOB_QUERY = 0, TK_JOB_MERGE = 1 };
@@ -70,8 +75,8 @@ int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit*
                      int* counts, cudaStream_t stream);
 
 // Shared-memory bytes of the two kernel families for a given in-smem eig order.
-size_t tk_stitch_smem_bytes(int dtype, int nsm);
+size_t tk_stitch_smem_bytes(int dtype, size_t arena);
 size_t tk_leaf_smem_bytes(int dtype, int nsm);
-int tk_occupancy(int dtype, int which /*0 leaf, 1 stitch*/, size_t smem);
+int tk_occupancy(int dtype, int which /*0 leaf, 1 stitch*/, size_t smem, int threads);
 
 enum { TK_DEV_ERR_WORKSPACE = 1, TK_DEV_ERR_HITS = 2, TK_DEV_ERR_RANGE = 3 };

@@ -1,9 +1,10 @@
 // Kernels of the range-query Tucker engine.
 //
 //  k_hitset  Algorithm 1 (Recall) over the implicit dyadic stream segment tree.
-//  k_stitch  one CTA per job; a job is a range query (Section 6.1: Recall,
-//            Eq. (partial-tucker), Algorithm 2) or the re-decomposition of a
-//            newly complete node from its two children (Algorithm 3, Stitch).
+//  k_stitch  one WARP per job, jobs taken from a dynamic queue; a job is a
+//            range query (Section 6.1: Recall, Eq. (partial-tucker),
+//            Algorithm 2) or the re-decomposition of a newly complete node
+//            from its two children (Algorithm 3, Stitch).
 //  k_leaf    one CTA per leaf block: Tucker-ALS (Section 2) of the raw block.
 //
 // Stitch runs in coefficient space.  Every V~_i^(1) has orthonormal columns
@@ -20,6 +21,12 @@
 // step).  The loop never touches D or L: they enter only through the QR of
 // Phi_n and the final factor assembly.  This is an exact rewrite: the result
 // is Algorithm 2's iterate, up to rounding order.
+//
+// A job's problems are tiny (eig orders ~ sum_i r_i, tensors of r^p
+// elements), so one warp owns a job and synchronizes with __syncwarp only;
+// thousands of queries of a batch run concurrently, one per resident warp.
+// Each eigenproblem of an ALS iteration is warm-started from the same mode's
+// eigenvectors of the previous iteration (or of the initialization).
 #include <cstdio>
 
 #include "tk_device.cuh"
@@ -31,26 +38,50 @@ struct HitRec {
   int level, partial;
   int64_t index, node_lo, node_hi, lo, hi, slot;
   int64_t toff;       // row offset t_{i-1} of the hit in U^(1)
-  int64_t core_off;   // workspace offset of H~_i (dims q)
-  int64_t slice_off;  // workspace offset of the partial slice (reflectors)
-  int64_t stau_off;   // workspace offset of its tau
+  void* core;         // H~_i (dims q)
+  void* slice;        // partial slice (reflectors), if partial
+  void* stau;         // its tau
   int q[TK_MAXP];     // ranks of H~_i
   int nr0;            // stored temporal rank of the node
   int koff[TK_MAXP];  // column offset of the hit's block in mode n's coefficient space
 };
+static_assert(sizeof(HitRec) <= TK_HITREC_BYTES, "HitRec grew: update TK_HITREC_BYTES");
 
-struct StitchCtx {
-  int nh, err, L_int;
+template <class S> struct StitchCtx {
+  int nh, err;
   int64_t L;
   int ro[TK_MAXP];
   int k[TK_MAXP];     // sum_i q_i[n]
   int c[TK_MAXP];     // coefficient dimension: k[0] for time, min(D_n, k_n) otherwise
   int qmax[TK_MAXP];
-  int64_t off_phi[TK_MAXP], off_tau[TK_MAXP], off_R[TK_MAXP], off_E[TK_MAXP];
-  int64_t off_K, off_b0, off_b1, off_N, off_W, off_G, off_A, off_V, off_w, off_cs, off_pq;
+  HitRec* hits;       // the job's hit records (shared-memory copy when it fits)
+  S *phi[TK_MAXP], *tau[TK_MAXP], *R[TK_MAXP], *E[TK_MAXP], *Vs[TK_MAXP];
+  S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs;
+  int* pq;
   int neig;           // largest eig order of the job
-  int eig_in_smem;
+  int smem_used;      // bytes of the shared arena in use
 };
+
+// Shared memory of one job group (a warp or a CTA): this header, then the
+// Jacobi arrays for orders up to nsm (pq, c, s, w, A, V).
+template <class S> struct WarpSm {
+  StitchCtx<S> ctx;
+  S red[40];
+  S sc[4];
+  int flag;
+  int job;
+  int nsw;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared bytes of one job group: the header, then `arena` bytes into which
+// the job places its hottest buffers (the rest goes to its global chunk).
+template <class S> __host__ __device__ inline size_t group_smem_bytes(size_t arena) {
+  return align16(sizeof(WarpSm<S>)) + align16(arena);
+}
+
+constexpr int kLeafHdr = 640;  // bytes reserved for the leaf kernel's shared header
 
 __device__ __forceinline__ int64_t node_lo_of(const TkTreeView& tv, int j, int64_t k) {
   return (k << j) * (int64_t)tv.B;
@@ -141,41 +172,32 @@ __device__ void stitch_ranks(int p, const int* rq, const int64_t* ext, const Hit
   }
 }
 
-template <class S> struct Smem {
-  HitRec hits[TK_MAXH];
-  StitchCtx ctx;
-  S red[40];
-  S sc[4];
-  int flag;
-  int pq[1];  // followed by the Jacobi arrays (see layout())
-};
-
 // W (ro_m x q) = E_m^T R_m[:, koff .. koff+q): both row-major in the workspace.
-template <class S>
+template <class G, class S>
 __device__ void proj_coef(const S* E, int cm, int rom, const S* R, int km, int koff, int q, S* W) {
-  gemm<S>(rom, q, cm, E, 1, rom, R + koff, km, 1, W, q, 1, false);
+  gemm<G, S>(rom, q, cm, E, 1, rom, R + koff, km, 1, W, q, 1, false);
 }
 
-// The job body shared by range queries and node merges.
-template <class S>
+// One stitch job, executed by one group G (a warp or a CTA).  ws is the
+// group's workspace chunk (ws_cap elements); the hit records occupy its
+// first TK_MAXH entries.
+template <class G, class S>
 __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t te, int mlevel, int64_t mindex,
-                           const int* rq, S* ws, int64_t ws_cap, int nsm, S* core_dst, S* u0_dst, int64_t ld0,
+                           const int* rq, S* ws, int64_t ws_cap, size_t arena_bytes, S* core_dst, S* u0_dst,
+                           int64_t ld0,
                            S* const* un_dst, const int64_t* ldn, int* ranks_dst, tk_query_info* info,
-                           int* status, unsigned char* smem_raw) {
-  Smem<S>& sm = *reinterpret_cast<Smem<S>*>(smem_raw);
-  StitchCtx& cx = sm.ctx;
-  HitRec* hits = sm.hits;
+                           int* status, unsigned char* wsm_raw) {
+  WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(wsm_raw);
+  StitchCtx<S>& cx = sm.ctx;
+  const long long t_start = clock64();
+  HitRec* hits = reinterpret_cast<HitRec*>(ws);  // Recall writes here; copied to the arena below
+  const int hits_elems = (int)((TK_MAXH * (int64_t)TK_HITREC_BYTES + sizeof(S) - 1) / sizeof(S));
   const int p = tv.p;
-  const int tid = threadIdx.x;
-  // Jacobi scratch in shared memory (after the fixed part).
-  const int half_cap = nsm / 2 + 2;
-  int* js_pq = sm.pq;
-  S* js_cs = reinterpret_cast<S*>(((uintptr_t)(js_pq + half_cap) + 15) & ~(uintptr_t)15);
-  S* js_w = js_cs + 2 * half_cap;
-  S* sA = js_w + nsm + 2;
-  S* sV = sA + (int64_t)nsm * nsm;
+  const int lane = G::rank();
+  const int nt = G::size();
+  unsigned char* arena = wsm_raw + align16(sizeof(WarpSm<S>));
 
-  if (tid == 0) {
+  if (lane == 0) {
     cx.err = 0;
     int nh = 0;
     if (mode == TK_JOB_QUERY) {
@@ -224,37 +246,57 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
       cx.qmax[n] = qm;
       cx.c[n] = (n == 0) ? kk : (tv.D[n] < kk ? tv.D[n] : kk);
     }
-    // workspace layout (bump allocation, 32-element aligned)
-    int64_t cur = 0;
-    auto take = [&](int64_t nel) {
-      const int64_t o = cur;
-      cur += (nel + 31) & ~(int64_t)31;
-      return o;
-    };
-    for (int i = 0; i < cx.nh; ++i) {
-      HitRec& h = hits[i];
-      int64_t cs = 1;
-      for (int n = 0; n < p; ++n) cs *= (h.q[n] > (n == 0 ? h.nr0 : h.q[n]) ? h.q[n] : (n == 0 ? h.nr0 : h.q[n]));
-      h.core_off = take(cs);
-      if (h.partial) {
-        h.slice_off = take((h.hi - h.lo) * (int64_t)h.nr0);
-        h.stau_off = take(h.nr0);
-      } else {
-        h.slice_off = h.stau_off = 0;
+    // Workspace layout: bump allocation in the group's shared arena first, in
+    // order of how often the buffer is touched, then in the global chunk
+    // (after the hit records).  Shared memory avoids the L2 round trip that
+    // every read-after-write of the global chunk costs.
+    size_t scur = 0;
+    int64_t cur = hits_elems;
+    auto take_bytes = [&](size_t bytes) -> void* {
+      bytes = (bytes + 127) & ~(size_t)127;
+      if (scur + bytes <= arena_bytes) {
+        void* q = arena + scur;
+        scur += bytes;
+        return q;
       }
+      void* q = ws + cur;
+      cur += (int64_t)((bytes + sizeof(S) - 1) / sizeof(S));
+      return q;
+    };
+    auto take = [&](int64_t nel) -> S* { return reinterpret_cast<S*>(take_bytes((size_t)nel * sizeof(S))); };
+    {
+      HitRec* hcopy = reinterpret_cast<HitRec*>(take_bytes(sizeof(HitRec) * (size_t)(cx.nh > 0 ? cx.nh : 1)));
+      for (int i = 0; i < cx.nh; ++i) hcopy[i] = hits[i];
+      cx.hits = hcopy;
     }
     int neig = cx.c[0];
-    for (int n = 1; n < p; ++n) {
-      cx.off_phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
-      cx.off_tau[n] = take(cx.k[n]);
-      cx.off_R[n] = take((int64_t)cx.c[n] * cx.k[n]);
-      cx.off_E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
+    for (int n = 1; n < p; ++n)
       if (cx.c[n] > neig) neig = cx.c[n];
+    cx.neig = neig;
+    cx.A = take((int64_t)neig * neig);
+    cx.V = take((int64_t)neig * neig);
+    cx.w = take(neig + 2);
+    cx.cs = take(2 * (neig / 2 + 2));
+    cx.pq = reinterpret_cast<int*>(take_bytes(sizeof(int) * (size_t)(neig / 2 + 2)));
+    cx.T = take((int64_t)neig * neig);
+    for (int n = 0; n < p; ++n) cx.Vs[n] = take((int64_t)cx.c[n] * cx.c[n]);
+    for (int n = 0; n < p; ++n) cx.E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
+    for (int n = 1; n < p; ++n) cx.R[n] = take((int64_t)cx.c[n] * cx.k[n]);
+    int wmax = tv.r[0] * tv.r[0];
+    for (int m = 0; m < p; ++m) {
+      const int v = cx.ro[m] * (cx.qmax[m] > 1 ? cx.qmax[m] : 1);
+      if (v > wmax) wmax = v;
     }
-    cx.off_E[0] = take((int64_t)cx.c[0] * cx.ro[0]);
-    int64_t Kel = cx.k[0];
-    for (int m = 1; m < p; ++m) Kel *= cx.ro[m];
-    cx.off_K = take(Kel);
+    cx.W = take(wmax);
+    int64_t gel = 1;
+    for (int n = 0; n < p; ++n) gel *= cx.ro[n];
+    cx.G = take(gel);
+    for (int i = 0; i < cx.nh; ++i) {
+      HitRec& h = cx.hits[i];
+      int64_t cs = 1;
+      for (int n = 0; n < p; ++n) cs *= (n == 0 ? (h.q[0] > h.nr0 ? h.q[0] : h.nr0) : h.q[n]);
+      h.core = take(cs);
+    }
     // chain buffers: every intermediate has, per mode, at most max(q_max, ro, nr0) (or c_n) entries
     int64_t tb = 0;
     for (int n = 0; n < p; ++n) {
@@ -267,52 +309,70 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
       }
       if (s > tb) tb = s;
     }
-    cx.off_b0 = take(tb);
-    cx.off_b1 = take(tb);
-    cx.off_N = take(tb);
-    int wmax = tv.r[0] * tv.r[0];
-    for (int m = 0; m < p; ++m) {
-      const int v = cx.ro[m] * (cx.qmax[m] > 1 ? cx.qmax[m] : 1);
-      if (v > wmax) wmax = v;
+    cx.b0 = take(tb);
+    cx.b1 = take(tb);
+    cx.N = take(tb);
+    int64_t Kel = cx.k[0];
+    for (int m = 1; m < p; ++m) Kel *= cx.ro[m];
+    cx.K = take(Kel);
+    for (int n = 1; n < p; ++n) {
+      cx.phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
+      cx.tau[n] = take(cx.k[n]);
     }
-    cx.off_W = take(wmax);
-    int64_t gel = 1;
-    for (int n = 0; n < p; ++n) gel *= cx.ro[n];
-    cx.off_G = take(gel);
-    cx.neig = neig;
-    cx.eig_in_smem = neig <= nsm;
-    if (!cx.eig_in_smem) {
-      cx.off_A = take((int64_t)neig * neig);
-      cx.off_V = take((int64_t)neig * neig);
-      cx.off_w = take(neig + 2);
-      cx.off_cs = take(2 * (neig / 2 + 2));
-      cx.off_pq = take(((neig / 2 + 2) * (int64_t)sizeof(int) + sizeof(S) - 1) / sizeof(S));
-    } else {
-      cx.off_A = cx.off_V = cx.off_w = cx.off_cs = cx.off_pq = 0;
+    for (int i = 0; i < cx.nh; ++i) {
+      HitRec& h = cx.hits[i];
+      if (h.partial) {
+        h.slice = take((h.hi - h.lo) * (int64_t)h.nr0);
+        h.stau = take(h.nr0);
+      } else {
+        h.slice = h.stau = nullptr;
+      }
     }
+    cx.smem_used = (int)scur;
     if (cur > ws_cap && cx.err == 0) cx.err = TK_DEV_ERR_WORKSPACE;
   }
-  __syncthreads();
+  G::sync();
   if (cx.err) {
-    if (tid == 0) {
+    if (lane == 0) {
       set_err(status, cx.err);
       if (info) {
         info->iters = -cx.err;
         info->n_hits = cx.nh;
       }
     }
+    G::sync();
     return;
   }
   const int nh = cx.nh;
-  S* A = cx.eig_in_smem ? sA : ws + cx.off_A;
-  S* V = cx.eig_in_smem ? sV : ws + cx.off_V;
-  S* wv = cx.eig_in_smem ? js_w : ws + cx.off_w;
-  if (!cx.eig_in_smem) {
-    js_cs = ws + cx.off_cs;
-    js_pq = reinterpret_cast<int*>(ws + cx.off_pq);
-  }
-  JacobiScratch js{js_pq, &sm.flag};
+  hits = cx.hits;
+  S* A = cx.A;
+  S* V = cx.V;
+  S* wv = cx.w;
+  JacobiScratch<S> js;
+  js.pq = cx.pq;
+  js.c = cx.cs;
+  js.s = cx.cs + (cx.neig / 2 + 2);
+  js.flag = &sm.flag;
+  js.red = sm.red;
+  js.nsw = &sm.nsw;
+  S* T = cx.T;
   const int maxsw = sizeof(S) == 8 ? 24 : 16;
+  bool have_v[TK_MAXP];
+  for (int n = 0; n < TK_MAXP; ++n) have_v[n] = false;
+  int sweeps = 0;
+  // eigenvectors of the order-nsz matrix in A, warm-started from the mode's previous basis
+  auto eig = [&](int mode_n, int nsz) {
+    S* Vs = cx.Vs[mode_n];
+    const bool warm = have_v[mode_n];
+    if (warm) {
+      for (int i = lane; i < nsz * nsz; i += nt) V[i] = Vs[i];
+      G::sync();
+    }
+    sweeps += jacobi_eig<G, S>(nsz, A, V, T, warm, wv, js, maxsw);
+    for (int i = lane; i < nsz * nsz; i += nt) Vs[i] = V[i];
+    G::sync();
+    have_v[mode_n] = true;
+  };
   int dims[TK_MAXP];
 
   // ---- hit decompositions: stored payloads or Eq. (partial-tucker) -------
@@ -321,99 +381,98 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
     const HitRec& h = hits[i];
     const S* core = reinterpret_cast<const S*>(tv.core_pool) + h.slot * tv.core_stride;
     const int* nr = tv.node_ranks + h.slot * TK_MAXP;
-    S* Hc = ws + h.core_off;
+    S* Hc = reinterpret_cast<S*>(h.core);
+    int qd[TK_MAXP];
+    for (int n = 0; n < p; ++n) qd[n] = h.q[n];
     if (!h.partial) {
-      int64_t tot = 1;
-      for (int n = 0; n < p; ++n) tot *= h.q[n];
-      for (int64_t idx = tid; idx < tot; idx += blockDim.x) {
-        int64_t rem = idx, src = 0, strd = 1;
+      int tot = 1;
+      for (int n = 0; n < p; ++n) tot *= qd[n];
+      for (int idx = lane; idx < tot; idx += nt) {
+        int rem = idx, src = 0, strd = 1;
         for (int n = p - 1; n >= 0; --n) {
-          const int in = (int)(rem % h.q[n]);
-          rem /= h.q[n];
+          const int in = rem % qd[n];
+          rem /= qd[n];
           src += in * strd;
           strd *= tv.r[n];
         }
         Hc[idx] = core[src];
       }
-      __syncthreads();
+      G::sync();
     } else {
       // slice rows of the node's temporal factor, QR, then H x_1 R~
-      const int64_t ell = h.hi - h.lo;
+      const int ell = (int)(h.hi - h.lo);
       const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride;
-      S* sl = ws + h.slice_off;
+      S* sl = reinterpret_cast<S*>(h.slice);
       const int nr0 = h.nr0;
-      for (int64_t idx = tid; idx < ell * nr0; idx += blockDim.x) {
-        const int64_t t = idx / nr0;
-        const int c = (int)(idx % nr0);
+      for (int idx = lane; idx < ell * nr0; idx += nt) {
+        const int t = idx / nr0, c = idx % nr0;
         sl[idx] = tf[(h.lo + t) * tv.r[0] + c];
       }
-      __syncthreads();
-      householder_qr<S>(sl, (int)ell, nr0, nr0, ws + h.stau_off, sm.sc);
-      // stored core (logical dims nr) into the chain buffer, then x_1 R~
-      int64_t tot = 1;
+      G::sync();
+      householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc);
+      int tot = 1;
       for (int n = 0; n < p; ++n) {
         dims[n] = nr[n];
         tot *= nr[n];
       }
-      S* b0 = ws + cx.off_b0;
-      for (int64_t idx = tid; idx < tot; idx += blockDim.x) {
-        int64_t rem = idx, src = 0, strd = 1;
+      S* b0 = cx.b0;
+      for (int idx = lane; idx < tot; idx += nt) {
+        int rem = idx, src = 0, strd = 1;
         for (int n = p - 1; n >= 0; --n) {
-          const int in = (int)(rem % dims[n]);
+          const int in = rem % dims[n];
           rem /= dims[n];
           src += in * strd;
           strd *= tv.r[n];
         }
         b0[idx] = core[src];
       }
-      // clean upper-triangular R~ (q0 x nr0) into W
-      S* Rt = ws + cx.off_W;
+      S* Rt = cx.W;
       const int q0 = h.q[0];
-      for (int idx = tid; idx < q0 * nr0; idx += blockDim.x) {
+      for (int idx = lane; idx < q0 * nr0; idx += nt) {
         const int a = idx / nr0, b = idx % nr0;
         Rt[idx] = (b >= a) ? sl[a * nr0 + b] : S(0);
       }
-      __syncthreads();
-      ttm<S>(b0, dims, p, 0, Rt, nr0, 1, q0, Hc, false);
+      G::sync();
+      ttm<G, S>(b0, dims, p, 0, Rt, nr0, 1, q0, Hc, false);
     }
-    int64_t tot = 1;
-    for (int n = 0; n < p; ++n) tot *= h.q[n];
-    hn2 += sum_squares<S>(Hc, tot, sm.red);
+    int tot = 1;
+    for (int n = 0; n < p; ++n) tot *= qd[n];
+    hn2 += sum_squares<G, S>(Hc, tot, sm.red);
   }
 
   // ---- non-temporal bases Phi_n = Q_n R_n, and the implicit HOSVD start ---
   for (int n = 1; n < p; ++n) {
     const int Dn = tv.D[n], kn = cx.k[n], cn = cx.c[n];
-    S* Phi = ws + cx.off_phi[n];
+    S* Phi = cx.phi[n];
     for (int i = 0; i < nh; ++i) {
       const HitRec& h = hits[i];
       const S* F = reinterpret_cast<const S*>(tv.fac_pool[n]) + h.slot * tv.fac_stride[n];
-      const int qn = h.q[n];
-      for (int idx = tid; idx < Dn * qn; idx += blockDim.x) {
+      const int qn = h.q[n], ko = h.koff[n];
+      for (int idx = lane; idx < Dn * qn; idx += nt) {
         const int d = idx / qn, c = idx % qn;
-        Phi[(int64_t)d * kn + h.koff[n] + c] = F[(int64_t)d * tv.r[n] + c];
+        Phi[d * kn + ko + c] = F[d * tv.r[n] + c];
       }
     }
-    __syncthreads();
-    householder_qr<S>(Phi, Dn, kn, kn, ws + cx.off_tau[n], sm.sc);
-    S* R = ws + cx.off_R[n];
-    for (int idx = tid; idx < cn * kn; idx += blockDim.x) {
+    G::sync();
+    householder_qr<G, S>(Phi, Dn, kn, kn, cx.tau[n], sm.sc);
+    S* R = cx.R[n];
+    for (int idx = lane; idx < cn * kn; idx += nt) {
       const int a = idx / kn, b = idx % kn;
-      R[idx] = (b >= a) ? Phi[(int64_t)a * kn + b] : S(0);
+      R[idx] = (b >= a) ? Phi[a * kn + b] : S(0);
     }
-    for (int idx = tid; idx < cn * cn; idx += blockDim.x) A[(idx / cn) * cn + idx % cn] = 0;
-    __syncthreads();
+    for (int idx = lane; idx < cn * cn; idx += nt) A[idx] = 0;
+    G::sync();
     // init: sum_i modegram_n(H~_i x_n R_n[:, blk i]) = Q_n^T mat_n(Y~) mat_n(Y~)^T Q_n
     for (int i = 0; i < nh; ++i) {
       const HitRec& h = hits[i];
       for (int m = 0; m < p; ++m) dims[m] = h.q[m];
-      S* b0 = ws + cx.off_b0;
-      ttm<S>(ws + h.core_off, dims, p, n, R + h.koff[n], kn, 1, cn, b0, false);
+      S* b0 = cx.b0;
+      ttm<G, S>(reinterpret_cast<S*>(h.core), dims, p, n, R + h.koff[n], kn, 1, cn, b0, false);
       dims[n] = cn;
-      mode_gram<S>(b0, dims, p, n, A, cn, true);
+      mode_gram<G, S>(b0, dims, p, n, A, cn, true);
     }
-    jacobi_eig<S>(cn, A, cn, V, cn, wv, js_cs, js, sm.red, maxsw);
-    select_top<S>(cn, wv, V, cn, cx.ro[n], ws + cx.off_E[n], cx.ro[n]);
+    eig(n, cn);
+    select_top<G, S>(cn, wv, V, cx.ro[n], cx.E[n], cx.ro[n]);
   }
 
   // ---- Algorithm 2 iterations --------------------------------------------
@@ -422,24 +481,24 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
   int it = 0;
   const int maxit = tv.max_iter > 0 ? tv.max_iter : 1;
   const int* ro = cx.ro;
-  S* K = ws + cx.off_K;
-  S* C = ws + cx.off_E[0];
-  S* N = ws + cx.off_N;
-  S* Wb = ws + cx.off_W;
-  S* b0 = ws + cx.off_b0;
-  S* b1 = ws + cx.off_b1;
+  S* K = cx.K;
+  S* C = cx.E[0];
+  S* N = cx.N;
+  S* Wb = cx.W;
+  S* b0 = cx.b0;
+  S* b1 = cx.b1;
   for (it = 1; it <= maxit; ++it) {
     // temporal mode, Eq. (stitch-temp-2) in coefficient space
-    int64_t krow = 1;
+    int krow = 1;
     for (int m = 1; m < p; ++m) krow *= ro[m];
     for (int i = 0; i < nh; ++i) {
       const HitRec& h = hits[i];
       for (int m = 0; m < p; ++m) dims[m] = h.q[m];
-      const S* src = ws + h.core_off;
+      const S* src = reinterpret_cast<S*>(h.core);
       for (int m = 1; m < p; ++m) {
-        proj_coef<S>(ws + cx.off_E[m], cx.c[m], ro[m], ws + cx.off_R[m], cx.k[m], h.koff[m], h.q[m], Wb);
-        S* dst = (m == p - 1) ? K + (int64_t)h.koff[0] * krow : ((m & 1) ? b0 : b1);
-        ttm<S>(src, dims, p, m, Wb, h.q[m], 1, ro[m], dst, false);
+        proj_coef<G, S>(cx.E[m], cx.c[m], ro[m], cx.R[m], cx.k[m], h.koff[m], h.q[m], Wb);
+        S* dst = (m == p - 1) ? K + h.koff[0] * krow : ((m & 1) ? b0 : b1);
+        ttm<G, S>(src, dims, p, m, Wb, h.q[m], 1, ro[m], dst, false);
         dims[m] = ro[m];
         src = dst;
       }
@@ -448,9 +507,9 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
       const int c0 = cx.c[0];
       dims[0] = c0;
       for (int m = 1; m < p; ++m) dims[m] = ro[m];
-      mode_gram<S>(K, dims, p, 0, A, c0, false);
-      jacobi_eig<S>(c0, A, c0, V, c0, wv, js_cs, js, sm.red, maxsw);
-      select_top<S>(c0, wv, V, c0, ro[0], C, ro[0]);
+      mode_gram<G, S>(K, dims, p, 0, A, c0, false);
+      eig(0, c0);
+      select_top<G, S>(c0, wv, V, ro[0], C, ro[0]);
     }
     // non-temporal modes, Eq. (stitch-nontemp-3) in coefficient space
     for (int n = 1; n < p; ++n) {
@@ -459,37 +518,37 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
         const HitRec& h = hits[i];
         for (int m = 0; m < p; ++m) dims[m] = h.q[m];
         // x_1 C_i^T : M(alpha, j) = C[(koff0 + j) * ro0 + alpha]
-        ttm<S>(ws + h.core_off, dims, p, 0, C + (int64_t)h.koff[0] * ro[0], 1, ro[0], ro[0], b0, false);
+        ttm<G, S>(reinterpret_cast<S*>(h.core), dims, p, 0, C + h.koff[0] * ro[0], 1, ro[0], ro[0], b0, false);
         dims[0] = ro[0];
         S* src = b0;
         S* other = b1;
         for (int m = 1; m < p; ++m) {
           if (m == n) continue;
-          proj_coef<S>(ws + cx.off_E[m], cx.c[m], ro[m], ws + cx.off_R[m], cx.k[m], h.koff[m], h.q[m], Wb);
-          ttm<S>(src, dims, p, m, Wb, h.q[m], 1, ro[m], other, false);
+          proj_coef<G, S>(cx.E[m], cx.c[m], ro[m], cx.R[m], cx.k[m], h.koff[m], h.q[m], Wb);
+          ttm<G, S>(src, dims, p, m, Wb, h.q[m], 1, ro[m], other, false);
           dims[m] = ro[m];
           S* t = src;
           src = other;
           other = t;
         }
-        ttm<S>(src, dims, p, n, ws + cx.off_R[n] + h.koff[n], kn, 1, cn, N, i > 0);
+        ttm<G, S>(src, dims, p, n, cx.R[n] + h.koff[n], kn, 1, cn, N, i > 0);
       }
       for (int m = 0; m < p; ++m) dims[m] = ro[m];
       dims[n] = cn;
-      mode_gram<S>(N, dims, p, n, A, cn, false);
-      jacobi_eig<S>(cn, A, cn, V, cn, wv, js_cs, js, sm.red, maxsw);
-      select_top<S>(cn, wv, V, cn, ro[n], ws + cx.off_E[n], ro[n]);
+      mode_gram<G, S>(N, dims, p, n, A, cn, false);
+      eig(n, cn);
+      select_top<G, S>(cn, wv, V, ro[n], cx.E[n], ro[n]);
     }
     // core: G = N_p x_p E_p^T (Algorithm 2's last step) and the stop test
     {
       const int n = p - 1;
       for (int m = 0; m < p; ++m) dims[m] = ro[m];
       dims[n] = cx.c[n];
-      ttm<S>(N, dims, p, n, ws + cx.off_E[n], 1, ro[n], ro[n], ws + cx.off_G, false);
+      ttm<G, S>(N, dims, p, n, cx.E[n], 1, ro[n], ro[n], cx.G, false);
     }
-    int64_t gel = 1;
+    int gel = 1;
     for (int m = 0; m < p; ++m) gel *= ro[m];
-    const S gn2 = sum_squares<S>(ws + cx.off_G, gel, sm.red);
+    const S gn2 = sum_squares<G, S>(cx.G, gel, sm.red);
     e = hn2 > S(0) ? sqrt(fmax(S(0), S(1) - gn2 / hn2)) : S(0);
     if (tv.tol > 0 && it > 1 && fabs(e - e_prev) < (S)tv.tol) break;
     e_prev = e;
@@ -498,61 +557,57 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
 
   // ---- outputs: core, U^(1) = blockdiag(V~_i^(1)) C, U^(n) = Q_n E_n --------
   {
-    int64_t ctot = 1, gel = 1;
-    for (int m = 0; m < p; ++m) {
-      ctot *= rq[m];
-      gel *= ro[m];
-    }
-    const S* G = ws + cx.off_G;
-    for (int64_t idx = tid; idx < ctot; idx += blockDim.x) {
-      int64_t rem = idx, src = 0, strd = 1;
+    int ctot = 1;
+    for (int m = 0; m < p; ++m) ctot *= rq[m];
+    const S* Gc = cx.G;
+    for (int idx = lane; idx < ctot; idx += nt) {
+      int rem = idx, src = 0, strd = 1;
       bool inside = true;
       for (int n = p - 1; n >= 0; --n) {
-        const int in = (int)(rem % rq[n]);
+        const int in = rem % rq[n];
         rem /= rq[n];
         if (in >= ro[n]) inside = false;
         src += in * strd;
         strd *= ro[n];
       }
-      core_dst[idx] = inside ? G[src] : S(0);
+      core_dst[idx] = inside ? Gc[src] : S(0);
     }
   }
   for (int i = 0; i < nh; ++i) {
     const HitRec& h = hits[i];
-    const int64_t ell = h.hi - h.lo;
+    const int ell = (int)(h.hi - h.lo);
     S* Y = u0_dst + h.toff * ld0;
-    const S* Ci = C + (int64_t)h.koff[0] * ro[0];
+    const S* Ci = C + h.koff[0] * ro[0];
     if (!h.partial) {
       const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride + h.lo * tv.r[0];
-      gemm<S>((int)ell, ro[0], h.q[0], tf, tv.r[0], 1, Ci, ro[0], 1, Y, ld0, 1, false);
+      gemm<G, S>(ell, ro[0], h.q[0], tf, tv.r[0], 1, Ci, ro[0], 1, Y, ld0, 1, false);
     } else {
-      for (int64_t idx = tid; idx < ell * ro[0]; idx += blockDim.x) {
-        const int64_t t = idx / ro[0];
-        const int a = (int)(idx % ro[0]);
+      for (int idx = lane; idx < ell * ro[0]; idx += nt) {
+        const int t = idx / ro[0], a = idx % ro[0];
         Y[t * ld0 + a] = (t < h.q[0]) ? Ci[t * ro[0] + a] : S(0);
       }
-      __syncthreads();
-      householder_apply_q<S>(ws + h.slice_off, (int)ell, h.q[0], h.nr0, ws + h.stau_off, Y, ro[0], ld0);
+      G::sync();
+      householder_apply_q<G, S>(reinterpret_cast<S*>(h.slice), ell, h.q[0], h.nr0, reinterpret_cast<S*>(h.stau), Y, ro[0], ld0);
     }
     if (ro[0] < rq[0]) {
       const int padc = rq[0] - ro[0];
-      for (int64_t idx = tid; idx < ell * padc; idx += blockDim.x) Y[(idx / padc) * ld0 + ro[0] + idx % padc] = 0;
+      for (int idx = lane; idx < ell * padc; idx += nt) Y[(idx / padc) * ld0 + ro[0] + idx % padc] = 0;
     }
-    __syncthreads();
+    G::sync();
   }
   for (int n = 1; n < p; ++n) {
     const int Dn = tv.D[n], cn = cx.c[n];
     S* Y = un_dst[n];
     const int64_t ld = ldn[n];
-    const S* E = ws + cx.off_E[n];
-    for (int64_t idx = tid; idx < (int64_t)Dn * rq[n]; idx += blockDim.x) {
-      const int d = (int)(idx / rq[n]), a = (int)(idx % rq[n]);
+    const S* E = cx.E[n];
+    for (int idx = lane; idx < Dn * rq[n]; idx += nt) {
+      const int d = idx / rq[n], a = idx % rq[n];
       Y[d * ld + a] = (a < ro[n] && d < cn) ? E[d * ro[n] + a] : S(0);
     }
-    __syncthreads();
-    householder_apply_q<S>(ws + cx.off_phi[n], Dn, cn, cx.k[n], ws + cx.off_tau[n], Y, ro[n], ld);
+    G::sync();
+    householder_apply_q<G, S>(cx.phi[n], Dn, cn, cx.k[n], cx.tau[n], Y, ro[n], ld);
   }
-  if (tid == 0) {
+  if (lane == 0) {
     if (ranks_dst)
       for (int n = 0; n < TK_MAXP; ++n) ranks_dst[n] = n < p ? ro[n] : 0;
     if (info) {
@@ -560,26 +615,45 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
       info->iters = it;
       info->n_hits = nh;
       info->fit_err = (double)e;
+      info->eig_sweeps = sweeps;
+      info->eig_max_order = cx.neig;
+      info->device_cycles = (int64_t)(clock64() - t_start);
     }
   }
-  __syncthreads();
+  G::sync();
 }
 
-template <class S>
+// Stitch kernel: each group (a warp or the whole CTA, per G) repeatedly
+// takes the next job index from the launch's queue counter (zeroed by the
+// host before the launch) and runs it.
+template <class S, class G>
 __global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int level, int64_t k0, int njobs,
                                                   TkQueryBatch qb, TkWorkspace wsd) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
-  for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
+  const int grp = G::size() == 32 ? (int)(threadIdx.x >> 5) : 0;
+  const int ngrp = G::size() == 32 ? (int)(blockDim.x >> 5) : 1;
+  const int tid = G::rank();
+  const size_t gbytes = group_smem_bytes<S>(wsd.smem_arena);
+  unsigned char* gsm = smem_raw + grp * gbytes;
+  WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(gsm);
+  const int64_t gid = (int64_t)blockIdx.x * ngrp + grp;
+  S* ws = reinterpret_cast<S*>(wsd.base) + gid * wsd.per_cta;
+  while (true) {
+    if (tid == 0) sm.job = (int)atomicAdd(wsd.counter, 1u);
+    G::sync();
+    const int job = sm.job;
+    G::sync();
+    if (job >= njobs) break;
     if (mode == TK_JOB_QUERY) {
       const int64_t ts = qb.ranges[2 * job], te = qb.ranges[2 * job + 1];
       S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[job];
       tk_query_info* info = qb.info ? qb.info + job : nullptr;
       if (!(ts >= 0 && ts < te && te <= tv.T)) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
           set_err(wsd.status, TK_DEV_ERR_RANGE);
           if (info) info->iters = -TK_DEV_ERR_RANGE;
         }
+        G::sync();
         continue;
       }
       int64_t ctot = 1;
@@ -593,8 +667,8 @@ __global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int l
         ldn[n] = qb.rq[n];
         cur += (int64_t)tv.D[n] * qb.rq[n];
       }
-      stitch_job<S>(tv, mode, ts, te, 0, 0, qb.rq, ws, wsd.per_cta, wsd.nsm, out, u0, qb.rq[0], un, ldn,
-                    nullptr, info, wsd.status, smem_raw);
+      stitch_job<G, S>(tv, mode, ts, te, 0, 0, qb.rq, ws, wsd.per_cta, wsd.smem_arena, out, u0, qb.rq[0], un,
+                       ldn, nullptr, info, wsd.status, gsm);
     } else {
       const int64_t k = k0 + job;
       const int64_t slot = tv.level_base[level] + k;
@@ -606,35 +680,37 @@ __global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int l
         un[n] = reinterpret_cast<S*>(tv.fac_pool[n]) + slot * tv.fac_stride[n];
         ldn[n] = tv.r[n];
       }
-      stitch_job<S>(tv, mode, 0, 0, level, k, tv.r, ws, wsd.per_cta, wsd.nsm, core, u0, tv.r[0], un, ldn,
-                    tv.node_ranks + slot * TK_MAXP, nullptr, wsd.status, smem_raw);
+      stitch_job<G, S>(tv, mode, 0, 0, level, k, tv.r, ws, wsd.per_cta, wsd.smem_arena, core, u0, tv.r[0], un,
+                       ldn, tv.node_ranks + slot * TK_MAXP, nullptr, wsd.status, gsm);
     }
-    __syncthreads();
   }
 }
 
-// ---- leaf blocks: Tucker-ALS of Section 2 on the raw block ---------------
+// ---- leaf blocks: Tucker-ALS of Section 2 on the raw block, one CTA each ----
 template <class S>
 __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int64_t block_stride,
                                                 int64_t first_block, int njobs, int ell, TkWorkspace wsd) {
+  using BG = BlockGroup;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   struct LeafSm {
     S red[40];
     S sc[4];
     int flag;
+    int nsw;
     int rl[TK_MAXP];
-    int64_t off_U[TK_MAXP], off_b0, off_b1, off_G, off_A, off_V, off_w, off_cs, off_pq;
+    int64_t off_U[TK_MAXP], off_Vs[TK_MAXP], off_b0, off_b1, off_G, off_T, off_A, off_V, off_w, off_cs, off_pq;
     int err, eig_in_smem;
   };
-  static_assert(sizeof(LeafSm) <= 512, "leaf shared header");
+  static_assert(sizeof(LeafSm) <= kLeafHdr, "leaf shared header");
   LeafSm& sm = *reinterpret_cast<LeafSm*>(smem_raw);
   const int nsm = wsd.nsm;
   const int half_cap = nsm / 2 + 2;
-  int* js_pq = reinterpret_cast<int*>(smem_raw + ((sizeof(LeafSm) + 15) & ~(size_t)15));
-  S* js_cs = reinterpret_cast<S*>(((uintptr_t)(js_pq + half_cap) + 15) & ~(uintptr_t)15);
-  S* js_w = js_cs + 2 * half_cap;
+  int* js_pq = reinterpret_cast<int*>(smem_raw + kLeafHdr);
+  S* js_c = reinterpret_cast<S*>(smem_raw + kLeafHdr + align16(half_cap * sizeof(int)));
+  S* js_s = js_c + half_cap;
+  S* js_w = js_s + half_cap;
   S* sA = js_w + nsm + 2;
-  S* sV = sA + (int64_t)nsm * nsm;
+  S* sV = sA + nsm * nsm;
   S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
   const int p = tv.p;
   const int tid = threadIdx.x;
@@ -671,6 +747,7 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
       int neig = 0;
       for (int n = 0; n < p; ++n) {
         sm.off_U[n] = take((int64_t)xd[n] * sm.rl[n]);
+        sm.off_Vs[n] = take((int64_t)xd[n] * xd[n]);
         if (xd[n] > neig) neig = xd[n];
       }
       int64_t xel = 1;
@@ -680,6 +757,7 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
       int64_t gel = 1;
       for (int n = 0; n < p; ++n) gel *= sm.rl[n];
       sm.off_G = take(gel);
+      sm.off_T = take((int64_t)neig * neig);
       sm.eig_in_smem = neig <= nsm;
       if (!sm.eig_in_smem) {
         sm.off_A = take((int64_t)neig * neig);
@@ -700,19 +778,47 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
     S* A = sm.eig_in_smem ? sA : ws + sm.off_A;
     S* V = sm.eig_in_smem ? sV : ws + sm.off_V;
     S* ew = sm.eig_in_smem ? js_w : ws + sm.off_w;
-    S* ecs = sm.eig_in_smem ? js_cs : ws + sm.off_cs;
-    JacobiScratch ejs{sm.eig_in_smem ? js_pq : reinterpret_cast<int*>(ws + sm.off_pq), &sm.flag};
+    JacobiScratch<S> js;
+    if (sm.eig_in_smem) {
+      js.pq = js_pq;
+      js.c = js_c;
+      js.s = js_s;
+    } else {
+      int neig = 0;
+      for (int n = 0; n < p; ++n) neig = xd[n] > neig ? xd[n] : neig;
+      js.pq = reinterpret_cast<int*>(ws + sm.off_pq);
+      js.c = ws + sm.off_cs;
+      js.s = ws + sm.off_cs + (neig / 2 + 2);
+    }
+    js.flag = &sm.flag;
+    js.red = sm.red;
+    js.nsw = &sm.nsw;
+    S* T = ws + sm.off_T;
+    bool have_v[TK_MAXP];
+    for (int n = 0; n < TK_MAXP; ++n) have_v[n] = false;
+    auto eig = [&](int mode_n, int nsz) {
+      S* Vs = ws + sm.off_Vs[mode_n];
+      const bool warm = have_v[mode_n];
+      if (warm) {
+        for (int i = tid; i < nsz * nsz; i += blockDim.x) V[i] = Vs[i];
+        __syncthreads();
+      }
+      jacobi_eig<BG, S>(nsz, A, V, T, warm, ew, js, maxsw);
+      for (int i = tid; i < nsz * nsz; i += blockDim.x) Vs[i] = V[i];
+      __syncthreads();
+      have_v[mode_n] = true;
+    };
     S* b0 = ws + sm.off_b0;
     S* b1 = ws + sm.off_b1;
     int64_t xel = 1;
     for (int n = 0; n < p; ++n) xel *= xd[n];
-    const S xn2 = sum_squares<S>(X, xel, sm.red);
+    const S xn2 = sum_squares<BG, S>(X, xel, sm.red);
     int dims[TK_MAXP];
     // HOSVD start for modes 2..p
     for (int n = 1; n < p; ++n) {
-      mode_gram<S>(X, xd, p, n, A, xd[n], false);
-      jacobi_eig<S>(xd[n], A, xd[n], V, xd[n], ew, ecs, ejs, sm.red, maxsw);
-      select_top<S>(xd[n], ew, V, xd[n], rl[n], ws + sm.off_U[n], rl[n]);
+      mode_gram<BG, S>(X, xd, p, n, A, xd[n], false);
+      eig(n, xd[n]);
+      select_top<BG, S>(xd[n], ew, V, rl[n], ws + sm.off_U[n], rl[n]);
     }
     S e_prev = S(-1), e = 0;
     int it;
@@ -727,19 +833,19 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
           S* dst;
           if (n == p && m == 0) dst = ws + sm.off_G;
           else dst = first ? b0 : (src == b0 ? b1 : b0);
-          ttm<S>(src, dims, p, m, ws + sm.off_U[m], 1, rl[m], rl[m], dst, false);
+          ttm<BG, S>(src, dims, p, m, ws + sm.off_U[m], 1, rl[m], rl[m], dst, false);
           dims[m] = rl[m];
           src = dst;
           first = false;
         }
         if (n == p) break;
-        mode_gram<S>(src, dims, p, n, A, xd[n], false);
-        jacobi_eig<S>(xd[n], A, xd[n], V, xd[n], ew, ecs, ejs, sm.red, maxsw);
-        select_top<S>(xd[n], ew, V, xd[n], rl[n], ws + sm.off_U[n], rl[n]);
+        mode_gram<BG, S>(src, dims, p, n, A, xd[n], false);
+        eig(n, xd[n]);
+        select_top<BG, S>(xd[n], ew, V, rl[n], ws + sm.off_U[n], rl[n]);
       }
       int64_t gel = 1;
       for (int m = 0; m < p; ++m) gel *= rl[m];
-      const S gn2 = sum_squares<S>(ws + sm.off_G, gel, sm.red);
+      const S gn2 = sum_squares<BG, S>(ws + sm.off_G, gel, sm.red);
       e = xn2 > S(0) ? sqrt(fmax(S(0), S(1) - gn2 / xn2)) : S(0);
       if (tv.tol > 0 && it > 1 && fabs(e - e_prev) < (S)tv.tol) break;
       e_prev = e;
@@ -747,34 +853,32 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
     // store: core (capacity dims r), temporal rows (ld r0), factors (ld r_n)
     {
       S* core = reinterpret_cast<S*>(tv.core_pool) + slot * tv.core_stride;
-      int64_t ctot = 1;
+      int ctot = 1;
       for (int m = 0; m < p; ++m) ctot *= tv.r[m];
-      const S* G = ws + sm.off_G;
-      for (int64_t idx = tid; idx < ctot; idx += blockDim.x) {
-        int64_t rem = idx, src = 0, strd = 1;
+      const S* Gc = ws + sm.off_G;
+      for (int idx = tid; idx < ctot; idx += blockDim.x) {
+        int rem = idx, src = 0, strd = 1;
         bool inside = true;
         for (int n = p - 1; n >= 0; --n) {
-          const int in = (int)(rem % tv.r[n]);
+          const int in = rem % tv.r[n];
           rem /= tv.r[n];
           if (in >= rl[n]) inside = false;
           src += in * strd;
           strd *= rl[n];
         }
-        core[idx] = inside ? G[src] : S(0);
+        core[idx] = inside ? Gc[src] : S(0);
       }
       S* tf = reinterpret_cast<S*>(tv.tfac) + b * (int64_t)tv.B * tv.r[0];
       const S* U0 = ws + sm.off_U[0];
-      for (int64_t idx = tid; idx < (int64_t)ell * tv.r[0]; idx += blockDim.x) {
-        const int64_t t = idx / tv.r[0];
-        const int c = (int)(idx % tv.r[0]);
+      for (int idx = tid; idx < ell * tv.r[0]; idx += blockDim.x) {
+        const int t = idx / tv.r[0], c = idx % tv.r[0];
         tf[idx] = c < rl[0] ? U0[t * rl[0] + c] : S(0);
       }
       for (int n = 1; n < p; ++n) {
         S* F = reinterpret_cast<S*>(tv.fac_pool[n]) + slot * tv.fac_stride[n];
         const S* Un = ws + sm.off_U[n];
-        for (int64_t idx = tid; idx < (int64_t)tv.D[n] * tv.r[n]; idx += blockDim.x) {
-          const int64_t d = idx / tv.r[n];
-          const int c = (int)(idx % tv.r[n]);
+        for (int idx = tid; idx < tv.D[n] * tv.r[n]; idx += blockDim.x) {
+          const int d = idx / tv.r[n], c = idx % tv.r[n];
           F[idx] = c < rl[n] ? Un[d * rl[n] + c] : S(0);
         }
       }
@@ -806,29 +910,20 @@ __global__ void k_hitset(TkTreeView tv, int n, const int64_t* ranges, tk_hit* ou
 
 using namespace tk;
 
-static size_t stitch_smem(size_t es, int nsm) {
-  const int half_cap = nsm / 2 + 2;
-  size_t fixed = offsetof(Smem<double>, pq);
-  if (es == 4) fixed = offsetof(Smem<float>, pq);
-  size_t b = fixed + half_cap * sizeof(int);
-  b = (b + 15) & ~(size_t)15;
-  b += es * (2 * half_cap + nsm + 2 + 2 * (size_t)nsm * nsm);
-  return b + 64;
-}
-
 static size_t leaf_smem(size_t es, int nsm) {
   const int half_cap = nsm / 2 + 2;
-  size_t fixed = 512;  // LeafSm (< 512 bytes), rounded
-  size_t b = fixed + half_cap * sizeof(int);
-  b = (b + 15) & ~(size_t)15;
+  size_t b = kLeafHdr + align16(half_cap * sizeof(int));
   b += es * (2 * half_cap + nsm + 2 + 2 * (size_t)nsm * nsm);
   return b + 64;
 }
 
-size_t tk_stitch_smem_bytes(int dtype, int nsm) { return stitch_smem(dtype == TK_F64 ? 8 : 4, nsm); }
+// Dynamic shared bytes of a k_stitch CTA (one job group per CTA).
+size_t tk_stitch_smem_bytes(int dtype, size_t arena) {
+  return dtype == TK_F64 ? group_smem_bytes<double>(arena) : group_smem_bytes<float>(arena);
+}
 size_t tk_leaf_smem_bytes(int dtype, int nsm) { return leaf_smem(dtype == TK_F64 ? 8 : 4, nsm); }
 
-template <class S> static const void* stitch_fn() { return (const void*)k_stitch<S>; }
+template <class S> static const void* stitch_fn() { return (const void*)k_stitch<S, BlockGroup>; }
 template <class S> static const void* leaf_fn() { return (const void*)k_leaf<S>; }
 
 static int set_smem_attr(const void* fn, size_t smem) {
@@ -837,12 +932,12 @@ static int set_smem_attr(const void* fn, size_t smem) {
   return TK_OK;
 }
 
-int tk_occupancy(int dtype, int which, size_t smem) {
+int tk_occupancy(int dtype, int which, size_t smem, int threads) {
   const void* fn = which == 0 ? (dtype == TK_F64 ? leaf_fn<double>() : leaf_fn<float>())
                               : (dtype == TK_F64 ? stitch_fn<double>() : stitch_fn<float>());
   if (set_smem_attr(fn, smem) != TK_OK) return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TK_NT, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) return 0;
   return nb;
 }
 
@@ -860,33 +955,31 @@ int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t blo
   return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
 
+static int launch_stitch(int dtype, const TkTreeView& tv, int mode, int level, int64_t k0, int njobs,
+                         const TkQueryBatch& qb, const TkWorkspace& ws, int grid, cudaStream_t stream) {
+  const size_t smem = tk_stitch_smem_bytes(dtype, ws.smem_arena);
+  if (cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), stream) != cudaSuccess) return TK_ERR_CUDA;
+  if (dtype == TK_F64) {
+    if (set_smem_attr(stitch_fn<double>(), smem)) return TK_ERR_CUDA;
+    k_stitch<double, BlockGroup><<<grid, 32 * ws.warps, smem, stream>>>(tv, mode, level, k0, njobs, qb, ws);
+  } else {
+    if (set_smem_attr(stitch_fn<float>(), smem)) return TK_ERR_CUDA;
+    k_stitch<float, BlockGroup><<<grid, 32 * ws.warps, smem, stream>>>(tv, mode, level, k0, njobs, qb, ws);
+  }
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+}
+
 int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int njobs, const TkWorkspace& ws,
                     int grid, cudaStream_t stream) {
   if (njobs <= 0) return TK_OK;
-  const size_t smem = tk_stitch_smem_bytes(dtype, ws.nsm);
   TkQueryBatch qb{};
-  if (dtype == TK_F64) {
-    if (set_smem_attr(stitch_fn<double>(), smem)) return TK_ERR_CUDA;
-    k_stitch<double><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_MERGE, level, k0, njobs, qb, ws);
-  } else {
-    if (set_smem_attr(stitch_fn<float>(), smem)) return TK_ERR_CUDA;
-    k_stitch<float><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_MERGE, level, k0, njobs, qb, ws);
-  }
-  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+  return launch_stitch(dtype, tv, TK_JOB_MERGE, level, k0, njobs, qb, ws, grid, stream);
 }
 
 int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, const TkWorkspace& ws, int grid,
                     cudaStream_t stream) {
   if (qb.n <= 0) return TK_OK;
-  const size_t smem = tk_stitch_smem_bytes(dtype, ws.nsm);
-  if (dtype == TK_F64) {
-    if (set_smem_attr(stitch_fn<double>(), smem)) return TK_ERR_CUDA;
-    k_stitch<double><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws);
-  } else {
-    if (set_smem_attr(stitch_fn<float>(), smem)) return TK_ERR_CUDA;
-    k_stitch<float><<<grid, TK_NT, smem, stream>>>(tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws);
-  }
-  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+  return launch_stitch(dtype, tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws, grid, stream);
 }
 
 int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap, int* counts,
