@@ -327,91 +327,141 @@ __device__ S jacobi_prepare(int n, S* A, S* V, S* T, bool warm, JacobiScratch<S>
   return Eps<S>::v() * sqrt(G::template sum<S>(a2, js.red));
 }
 
+// Pair k of round rd of the round-robin ordering on m indices (m even):
+// pair 0 is (rd, m-1), pair k > 0 is (rd + k, rd - k) modulo m - 1.
+__device__ __forceinline__ void rr_pair(int rd, int k, int m, int& pp, int& qq) {
+  int a, b;
+  if (k == 0) {
+    a = rd;
+    b = m - 1;
+  } else {
+    a = rd + k;
+    if (a >= m - 1) a -= m - 1;
+    b = rd - k;
+    if (b < 0) b += m - 1;
+  }
+  pp = a < b ? a : b;
+  qq = a < b ? b : a;
+}
+
+// One round applies the n/2 disjoint rotations of its pairs at once: for
+// every 2x2 block (pair k's rows, pair l's columns) the new block is
+// R_k^T B R_l with R = [c s; -s c] (the row update J^T A followed by the
+// column update A J of each rotation), written together with its transpose;
+// V's rows are updated by the column rotations.  Each element of A is read
+// and written once per round and a round needs two barriers.
 template <class G, class S>
 __device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch<S> js, int max_sweeps) {
   const int tid = G::rank(), nt = G::size();
   const S eps = Eps<S>::v();
   const int m = n + (n & 1), half = m / 2;
-  // (pair k, column j) of element idx = k n + j, walked by carries
-  const int dk = nt / (n > 0 ? n : 1), dj = nt - dk * n;
-  const int k0 = tid / (n > 0 ? n : 1), j0 = tid - k0 * n;
+  const int nblk = half * (half + 1) / 2;
+  const S floor2 = floor_abs * floor_abs, eps2 = eps * eps;
+  // packed upper triangle of blocks (k <= l): walk start for this thread
+  int bk0 = 0, bl0 = 0;
+  if (tid < nblk) {
+    int a = (int)((2.f * half + 1.f - sqrtf((2.f * half + 1.f) * (2.f * half + 1.f) - 8.f * tid)) * 0.5f);
+    if (a < 0) a = 0;
+    while (a > 0 && a * (2 * half - a + 1) / 2 > tid) --a;
+    while ((a + 1) * (2 * half - a) / 2 <= tid) ++a;
+    bk0 = a;
+    bl0 = tid - a * (2 * half - a + 1) / 2 + a;
+  }
+  // (row i, pair l) of V: walk start and stride
+  const int vdl = nt / half, vdj = nt - vdl * half;  // element e = i * half + l
+  const int vi0 = tid / half, vl0 = tid - (tid / half) * half;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *js.flag = 0;
     G::sync();
     for (int rd = 0; rd < m - 1; ++rd) {
       for (int k = tid; k < half; k += nt) {
-        int a, b;
-        if (k == 0) {
-          a = rd;
-          b = m - 1;
-        } else {
-          a = rd + k;
-          if (a >= m - 1) a -= m - 1;
-          b = rd - k;
-          if (b < 0) b += m - 1;
-        }
-        const int pp = a < b ? a : b, qq = a < b ? b : a;
-        int code = -1;
+        int pp, qq;
+        rr_pair(rd, k, m, pp, qq);
         S c = 1, s = 0;
+        int rot = 0;
         if (qq < n) {
           const S apq = A[pp * n + qq];
           const S app = A[pp * n + pp], aqq = A[qq * n + qq];
-          const S aapq = fabs(apq);
-          if (aapq > floor_abs && aapq > eps * sqrt(fabs(app * aqq))) {
+          const S apq2 = apq * apq;
+          if (apq2 > floor2 && apq2 > eps2 * fabs(app * aqq)) {
             const S theta = (aqq - app) / (S(2) * apq);
             S t;
             if (fabs(theta) > S(1e15)) t = S(0.5) / theta;
             else t = (theta >= S(0) ? S(1) : S(-1)) / (fabs(theta) + sqrt(S(1) + theta * theta));
             c = S(1) / sqrt(S(1) + t * t);
             s = t * c;
-            code = pp | (qq << 16);
+            rot = 1;
             *js.flag = 1;
           }
         }
-        js.pq[k] = code;
+        js.pq[k] = pp | (qq << 12) | (rot << 24);
         js.c[k] = c;
         js.s[k] = s;
       }
       G::sync();
-      for (int idx = tid, k = k0, j = j0; idx < half * n; idx += nt) {
-        const int code = js.pq[k];
-        if (code >= 0) {
-          const int pp = code & 0xffff, qq = code >> 16;
-          const S c = js.c[k], s = js.s[k];
-          const S apj = A[pp * n + j], aqj = A[qq * n + j];
-          A[pp * n + j] = c * apj - s * aqj;
-          A[qq * n + j] = s * apj + c * aqj;
+      for (int b = tid, k = bk0, l = bl0; b < nblk; b += nt) {
+        const int ck = js.pq[k], cl = js.pq[l];
+        if ((ck | cl) >> 24) {
+          const int pk = ck & 0xfff, qk = (ck >> 12) & 0xfff, pl = cl & 0xfff, ql = (cl >> 12) & 0xfff;
+          const S c1 = js.c[k], s1 = js.s[k], c2 = js.c[l], s2 = js.s[l];
+          const bool vq = qk < n, vr = ql < n;
+          const S b00 = A[pk * n + pl];
+          const S b01 = vr ? A[pk * n + ql] : S(0);
+          const S b10 = vq ? A[qk * n + pl] : S(0);
+          const S b11 = (vq && vr) ? A[qk * n + ql] : S(0);
+          // rows: R_k^T B
+          const S r00 = c1 * b00 - s1 * b10, r01 = c1 * b01 - s1 * b11;
+          const S r10 = s1 * b00 + c1 * b10, r11 = s1 * b01 + c1 * b11;
+          // columns: (R_k^T B) R_l
+          S n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
+          S n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
+          if (k == l) {  // the annihilated pair
+            if (ck >> 24) n01 = n10 = S(0);
+            A[pk * n + pk] = n00;
+            if (vq) {
+              A[pk * n + qk] = n01;
+              A[qk * n + pk] = n10;
+              A[qk * n + qk] = n11;
+            }
+          } else {
+            A[pk * n + pl] = n00;
+            A[pl * n + pk] = n00;
+            if (vr) {
+              A[pk * n + ql] = n01;
+              A[ql * n + pk] = n01;
+            }
+            if (vq) {
+              A[qk * n + pl] = n10;
+              A[pl * n + qk] = n10;
+            }
+            if (vq && vr) {
+              A[qk * n + ql] = n11;
+              A[ql * n + qk] = n11;
+            }
+          }
         }
-        j += dj;
-        k += dk;
-        if (j >= n) {
-          j -= n;
+        l += nt;
+        while (l >= half && k < half - 1) {
+          l -= half - (k + 1);
           ++k;
         }
       }
-      G::sync();
-      for (int idx = tid, k = k0, i = j0; idx < half * n; idx += nt) {
-        const int kk = k, ii = i;
-        i += dj;
-        k += dk;
-        if (i >= n) {
-          i -= n;
-          ++k;
+      for (int e = tid, i = vi0, l = vl0; e < n * half; e += nt) {
+        const int cl = js.pq[l];
+        if (cl >> 24) {
+          const int pl = cl & 0xfff, ql = (cl >> 12) & 0xfff;
+          const S c2 = js.c[l], s2 = js.s[l];
+          const S vp = V[i * n + pl], vq = V[i * n + ql];
+          V[i * n + pl] = c2 * vp - s2 * vq;
+          V[i * n + ql] = s2 * vp + c2 * vq;
         }
-        const int code = js.pq[kk];
-        if (code < 0) continue;
-        const int pp = code & 0xffff, qq = code >> 16;
-        const S c = js.c[kk], s = js.s[kk];
-        const S aip = A[ii * n + pp], aiq = A[ii * n + qq];
-        S nip = c * aip - s * aiq, niq = s * aip + c * aiq;
-        if (ii == pp) niq = 0;
-        if (ii == qq) nip = 0;
-        A[ii * n + pp] = nip;
-        A[ii * n + qq] = niq;
-        const S vip = V[ii * n + pp], viq = V[ii * n + qq];
-        V[ii * n + pp] = c * vip - s * viq;
-        V[ii * n + qq] = s * vip + c * viq;
+        l += vdj;
+        i += vdl;
+        if (l >= half) {
+          l -= half;
+          ++i;
+        }
       }
       G::sync();
     }
@@ -424,21 +474,10 @@ __device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch
   return sweep;
 }
 
-// The whole eigendecomposition by group G.  Orders up to 32 run their sweeps
-// on the group's first warp alone (warp-synchronous rounds, no block-wide
-// barrier per round); larger orders use every thread of G.  Returns the
-// sweeps run.
+// The whole eigendecomposition by group G.  Returns the sweeps run.
 template <class G, class S>
 __device__ int jacobi_eig(int n, S* A, S* V, S* T, bool warm, S* w, JacobiScratch<S> js, int max_sweeps) {
   const S floor_abs = jacobi_prepare<G, S>(n, A, V, T, warm, js);
-  if (G::size() > 32 && n <= 32) {
-    if ((G::rank() >> 5) == 0) {
-      const int sw = jacobi_sweeps<WarpGroup, S>(n, A, V, floor_abs, w, js, max_sweeps);
-      if (G::rank() == 0) *js.nsw = sw;
-    }
-    G::sync();
-    return *js.nsw;
-  }
   return jacobi_sweeps<G, S>(n, A, V, floor_abs, w, js, max_sweeps);
 }
 

@@ -58,7 +58,7 @@ struct tk_tree {
   int nsm_stitch = 0, nsm_leaf = 0;
   int sm_count = 0;
   // staging for host io and batch metadata
-  DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf;
+  DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
   int64_t launches = 0;
 };
 
@@ -285,14 +285,14 @@ int max_hits(const tk_tree* t, int64_t nbt) {
 
 // Largest eig order kept in shared memory for each kernel family.
 // One CTA of stitch_warps() warps runs one stitch job at a time; the job
-// places its hottest buffers in a shared arena of this many bytes (four CTAs
+// places its hottest buffers in a shared arena of this many bytes (two CTAs
 // per SM) and the rest in its global workspace chunk.
 int pick_nsm_stitch(const tk_tree* t) {
   (void)t;
-  return 44 * 1024;
+  return 96 * 1024;
 }
 
-int stitch_warps(const tk_tree* t) { (void)t; return 4; }
+int stitch_warps(const tk_tree* t) { (void)t; return 8; }
 
 int pick_nsm_leaf(const tk_tree* t) {
   int need = t->cfg.leaf_slices;
@@ -498,7 +498,8 @@ void tk_tree_destroy(tk_tree* t) {
   DeviceGuard g(t->dev);
   if (t->stream) cudaStreamSynchronize(t->stream);
   DevBuf* bufs[] = {&t->core_pool, &t->tfac, &t->node_ranks, &t->tail_raw, &t->ws_stitch, &t->ws_leaf,
-                    &t->status, &t->stage_in, &t->stage_out, &t->stage_meta, &t->stage_info, &t->hit_buf};
+                    &t->status, &t->stage_in, &t->stage_out, &t->stage_meta, &t->stage_info, &t->hit_buf,
+                    &t->plan};
   for (DevBuf* b : bufs) dfree(*b);
   for (int n = 0; n < TK_MAXP; ++n) dfree(t->fac_pool[n]);
   if (t->own_stream && t->stream) cudaStreamDestroy(t->stream);
@@ -701,7 +702,16 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
   qb.offsets = d_offsets;
   qb.out = d_out;
   qb.info = d_info;
+  qb.order = nullptr;
   for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
+  if (n > 1) {  // longest-first schedule: heavy queries must not start last
+    rc = dalloc(t->plan, sizeof(int) * (size_t)n);
+    if (rc) return rc;
+    rc = tk_launch_plan(make_view(t), n, d_ranges, (int*)t->plan.ptr, t->stream);
+    t->launches += 1;
+    if (rc) return rc;
+    qb.order = (const int*)t->plan.ptr;
+  }
   rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
   t->launches += 1;
   if (rc) return rc;

@@ -60,6 +60,7 @@ struct TkQueryBatch {
   const int64_t* offsets;  // device, n+1
   void* out;               // device
   tk_query_info* info;     // device, n (may be null)
+  const int* order;        // device, n: processing order (may be null: index order)
   int rq[TK_MAXP];         // requested ranks
 };
 
@@ -71,6 +72,7 @@ int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int 
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
 int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
+int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int* order, cudaStream_t stream);
 int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap,
                      int* counts, cudaStream_t stream);
 

@@ -139,6 +139,46 @@ __device__ int recall_dev(const TkTreeView& tv, int64_t ts, int64_t te, HitRec* 
   return nh;
 }
 
+// Size of Algorithm 1's hit set (same traversal as recall_dev, no records).
+__device__ int recall_count(const TkTreeView& tv, int64_t ts, int64_t te) {
+  if (tv.height <= 0 || !(ts >= 0 && ts < te && te <= tv.T)) return 0;
+  int sj[2 * TK_MAXL + 4];
+  int64_t sk[2 * TK_MAXL + 4];
+  int sp = 1, nh = 0;
+  sj[0] = tv.height - 1;
+  sk[0] = 0;
+  while (sp > 0) {
+    --sp;
+    const int j = sj[sp];
+    const int64_t k = sk[sp];
+    const int64_t w = ((int64_t)1 << j) * tv.B;
+    const int64_t lo = k * w;
+    int64_t hi = lo + w;
+    if (hi > tv.T) hi = tv.T;
+    const int64_t a = ts > lo ? ts : lo, b = te < hi ? te : hi;
+    const int64_t ov = b > a ? b - a : 0;
+    const bool complete = ((k + 1) << j) <= tv.nb;
+    bool hit = false;
+    if (j == 0) hit = (k < tv.nbt) && ov > 0;
+    else if (complete) hit = (int64_t)tv.theta_den * ov >= (int64_t)tv.theta_num * (hi - lo);
+    if (hit) {
+      ++nh;
+      continue;
+    }
+    if (j == 0) continue;
+    const int64_t mu = (2 * k + 1) * (w / 2);
+    if (te <= mu) {
+      sj[sp] = j - 1; sk[sp] = 2 * k; ++sp;
+    } else if (ts >= mu) {
+      sj[sp] = j - 1; sk[sp] = 2 * k + 1; ++sp;
+    } else {
+      sj[sp] = j - 1; sk[sp] = 2 * k + 1; ++sp;
+      sj[sp] = j - 1; sk[sp] = 2 * k; ++sp;
+    }
+  }
+  return nh;
+}
+
 __device__ void set_err(int* status, int code) { atomicCAS(status, 0, code); }
 
 // Output-rank clamp of a stitch: r_n' = min(r_n, extent_n, sum_i min(q_in,
@@ -279,24 +319,6 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
     cx.cs = take(2 * (neig / 2 + 2));
     cx.pq = reinterpret_cast<int*>(take_bytes(sizeof(int) * (size_t)(neig / 2 + 2)));
     cx.T = take((int64_t)neig * neig);
-    for (int n = 0; n < p; ++n) cx.Vs[n] = take((int64_t)cx.c[n] * cx.c[n]);
-    for (int n = 0; n < p; ++n) cx.E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
-    for (int n = 1; n < p; ++n) cx.R[n] = take((int64_t)cx.c[n] * cx.k[n]);
-    int wmax = tv.r[0] * tv.r[0];
-    for (int m = 0; m < p; ++m) {
-      const int v = cx.ro[m] * (cx.qmax[m] > 1 ? cx.qmax[m] : 1);
-      if (v > wmax) wmax = v;
-    }
-    cx.W = take(wmax);
-    int64_t gel = 1;
-    for (int n = 0; n < p; ++n) gel *= cx.ro[n];
-    cx.G = take(gel);
-    for (int i = 0; i < cx.nh; ++i) {
-      HitRec& h = cx.hits[i];
-      int64_t cs = 1;
-      for (int n = 0; n < p; ++n) cs *= (n == 0 ? (h.q[0] > h.nr0 ? h.q[0] : h.nr0) : h.q[n]);
-      h.core = take(cs);
-    }
     // chain buffers: every intermediate has, per mode, at most max(q_max, ro, nr0) (or c_n) entries
     int64_t tb = 0;
     for (int n = 0; n < p; ++n) {
@@ -315,6 +337,24 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
     int64_t Kel = cx.k[0];
     for (int m = 1; m < p; ++m) Kel *= cx.ro[m];
     cx.K = take(Kel);
+    int wmax = tv.r[0] * tv.r[0];
+    for (int m = 0; m < p; ++m) {
+      const int v = cx.ro[m] * (cx.qmax[m] > 1 ? cx.qmax[m] : 1);
+      if (v > wmax) wmax = v;
+    }
+    cx.W = take(wmax);
+    int64_t gel = 1;
+    for (int n = 0; n < p; ++n) gel *= cx.ro[n];
+    cx.G = take(gel);
+    for (int n = 0; n < p; ++n) cx.E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
+    for (int n = 1; n < p; ++n) cx.R[n] = take((int64_t)cx.c[n] * cx.k[n]);
+    for (int i = 0; i < cx.nh; ++i) {
+      HitRec& h = cx.hits[i];
+      int64_t cs = 1;
+      for (int n = 0; n < p; ++n) cs *= (n == 0 ? (h.q[0] > h.nr0 ? h.q[0] : h.nr0) : h.q[n]);
+      h.core = take(cs);
+    }
+    for (int n = 0; n < p; ++n) cx.Vs[n] = take((int64_t)cx.c[n] * cx.c[n]);
     for (int n = 1; n < p; ++n) {
       cx.phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
       cx.tau[n] = take(cx.k[n]);
@@ -645,9 +685,10 @@ __global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int l
     G::sync();
     if (job >= njobs) break;
     if (mode == TK_JOB_QUERY) {
-      const int64_t ts = qb.ranges[2 * job], te = qb.ranges[2 * job + 1];
-      S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[job];
-      tk_query_info* info = qb.info ? qb.info + job : nullptr;
+      const int q = qb.order ? qb.order[job] : job;
+      const int64_t ts = qb.ranges[2 * q], te = qb.ranges[2 * q + 1];
+      S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[q];
+      tk_query_info* info = qb.info ? qb.info + q : nullptr;
       if (!(ts >= 0 && ts < te && te <= tv.T)) {
         if (tid == 0) {
           set_err(wsd.status, TK_DEV_ERR_RANGE);
@@ -888,6 +929,36 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
   }
 }
 
+// Longest-first processing order of a query batch: queries sorted by
+// decreasing hit-set size (a proxy of their cost: the eigenproblem orders
+// grow with it), by a counting sort in one CTA.  Ties keep no particular order;
+// the order only schedules work (every query writes its own outputs).
+__global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, int* order) {
+  constexpr int NB = TK_MAXH + 1;
+  __shared__ int hist[NB];
+  __shared__ int base[NB];
+  for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    int c = recall_count(tv, ranges[2 * q], ranges[2 * q + 1]);
+    atomicAdd(&hist[c < NB ? c : NB - 1], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = NB - 1; b >= 0; --b) {
+      base[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    int c = recall_count(tv, ranges[2 * q], ranges[2 * q + 1]);
+    const int pos = atomicAdd(&base[c < NB ? c : NB - 1], 1);
+    order[pos] = q;
+  }
+}
+
 __global__ void k_hitset(TkTreeView tv, int n, const int64_t* ranges, tk_hit* out, int cap, int* counts) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
@@ -980,6 +1051,12 @@ int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, con
                     cudaStream_t stream) {
   if (qb.n <= 0) return TK_OK;
   return launch_stitch(dtype, tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws, grid, stream);
+}
+
+int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int* order, cudaStream_t stream) {
+  if (n <= 0) return TK_OK;
+  k_plan<<<1, 1024, 0, stream>>>(tv, n, ranges, order);
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
 
 int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap, int* counts,
