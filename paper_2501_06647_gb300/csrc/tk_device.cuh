@@ -278,6 +278,7 @@ template <class S> struct JacobiScratch {
   int* flag;  // 1
   S* red;     // group reduction scratch
   int* nsw;   // 1: sweeps of the last call
+  S* thr;     // 1: bottom-block threshold of the current sweep
 };
 
 // Symmetric eigendecomposition of the n x n matrix A (leading dimension n)
@@ -293,8 +294,19 @@ template <class S> struct JacobiScratch {
 // orthonormal eigenvectors of the input A as columns and w the eigenvalues.
 // A rotation is skipped when |a_pq| <= eps sqrt(|a_pp a_qq|) or
 // |a_pq| <= eps ||A||_F (an entry at the rounding level of A moves no
-// eigenvector by more than rounding); the sweeps stop after one in which
-// every rotation was skipped, or after max_sweeps.
+// eigenvector by more than rounding).  Cyclic Jacobi converges quadratically,
+// so after a sweep in which every rotation had |a_pq| < 0.1 sqrt(eps)
+// sqrt(|a_pp a_qq|) the off-diagonal part left is below the rounding level:
+// the sweeps stop after such a sweep (its small rotations are applied), or
+// after max_sweeps.
+//
+// Only the r leading eigenvectors are wanted.  A is positive semidefinite
+// (a Gram matrix), so |a_pq| <= sqrt(a_pp a_qq) and the block of indices
+// whose diagonal lies below thr = sqrt(eps) * (r-th largest diagonal) has all
+// its eigenvalues below (n - r) thr: rotations of two such indices move no
+// vector of the leading-r invariant subspace, and are skipped (the threshold
+// is re-evaluated at the start of every sweep).  Pairs involving any other
+// index are still driven to the rounding level.
 //
 // jacobi_prepare does the warm transform (or V = I) and returns the absolute
 // skip floor; jacobi_sweeps runs the sweeps.  Both are executed by group G.
@@ -351,7 +363,7 @@ __device__ __forceinline__ void rr_pair(int rd, int k, int m, int& pp, int& qq) 
 // V's rows are updated by the column rotations.  Each element of A is read
 // and written once per round and a round needs two barriers.
 template <class G, class S>
-__device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch<S> js, int max_sweeps) {
+__device__ int jacobi_sweeps(int n, int r, S* A, S* V, S floor_abs, S* w, JacobiScratch<S> js, int max_sweeps) {
   const int tid = G::rank(), nt = G::size();
   const S eps = Eps<S>::v();
   const int m = n + (n & 1), half = m / 2;
@@ -371,9 +383,26 @@ __device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch
   const int vdl = nt / half, vdj = nt - vdl * half;  // element e = i * half + l
   const int vi0 = tid / half, vl0 = tid - (tid / half) * half;
   int sweep = 0;
+  const S sqeps = sqrt(eps);
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) *js.flag = 0;
+    if (tid == 0) {
+      *js.flag = 0;
+      *js.thr = S(-1);
+    }
     G::sync();
+    if (r > 0 && r < n) {  // thr = sqrt(eps) * (r-th largest diagonal)
+      for (int i = tid; i < n; i += nt) {
+        const S di = A[i * n + i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+          const S dj = A[j * n + j];
+          if (dj > di || (dj == di && j < i)) ++rank;
+        }
+        if (rank == r - 1) *js.thr = sqeps * fabs(di);
+      }
+      G::sync();
+    }
+    const S thr = *js.thr;
     for (int rd = 0; rd < m - 1; ++rd) {
       for (int k = tid; k < half; k += nt) {
         int pp, qq;
@@ -384,7 +413,8 @@ __device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch
           const S apq = A[pp * n + qq];
           const S app = A[pp * n + pp], aqq = A[qq * n + qq];
           const S apq2 = apq * apq;
-          if (apq2 > floor2 && apq2 > eps2 * fabs(app * aqq)) {
+          const bool bottom = app < thr && aqq < thr && fabs(apq) < thr;
+          if (!bottom && apq2 > floor2 && apq2 > eps2 * fabs(app * aqq)) {
             const S theta = (aqq - app) / (S(2) * apq);
             S t;
             if (fabs(theta) > S(1e15)) t = S(0.5) / theta;
@@ -392,7 +422,7 @@ __device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch
             c = S(1) / sqrt(S(1) + t * t);
             s = t * c;
             rot = 1;
-            *js.flag = 1;
+            if (apq2 > S(0.01) * eps * fabs(app * aqq)) *js.flag = 1;
           }
         }
         js.pq[k] = pp | (qq << 12) | (rot << 24);
@@ -475,10 +505,11 @@ __device__ int jacobi_sweeps(int n, S* A, S* V, S floor_abs, S* w, JacobiScratch
 }
 
 // The whole eigendecomposition by group G.  Returns the sweeps run.
+// r: number of leading eigenvectors the caller keeps (r >= n: all of them).
 template <class G, class S>
-__device__ int jacobi_eig(int n, S* A, S* V, S* T, bool warm, S* w, JacobiScratch<S> js, int max_sweeps) {
+__device__ int jacobi_eig(int n, int r, S* A, S* V, S* T, bool warm, S* w, JacobiScratch<S> js, int max_sweeps) {
   const S floor_abs = jacobi_prepare<G, S>(n, A, V, T, warm, js);
-  return jacobi_sweeps<G, S>(n, A, V, floor_abs, w, js, max_sweeps);
+  return jacobi_sweeps<G, S>(n, r, A, V, floor_abs, w, js, max_sweeps);
 }
 
 // E (n x r, leading dimension lde) <- the eigenvectors (columns of V, n x n)

@@ -59,6 +59,9 @@ struct tk_tree {
   int sm_count = 0;
   // staging for host io and batch metadata
   DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
+  // heavy queries of a batch run on a second, high-priority stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_plan = nullptr, ev_heavy = nullptr;
   int64_t launches = 0;
 };
 
@@ -331,6 +334,17 @@ int ensure_ws_leaf(tk_tree* t, int want_ctas) {
   return TK_OK;
 }
 
+// Heavy queries (hit sets of at least heavy_hits() nodes, eigenproblem orders
+// >= ~45) run in CTAs of heavy_warps() warps with a shared arena of
+// heavy_arena() bytes (one CTA per SM), concurrently with the light ones.
+int heavy_hits(const tk_tree* t) {
+  int r = 1;
+  for (int n = 0; n < t->p; ++n) r = std::max(r, t->cfg.ranks[n]);
+  return std::max(3, (45 + r - 1) / r);
+}
+int heavy_warps(const tk_tree* t) { (void)t; return 16; }
+size_t heavy_arena(const tk_tree* t) { (void)t; return 200 * 1024; }
+
 TkWorkspace ws_view(const tk_tree* t, bool leaf) {
   TkWorkspace w{};
   w.base = leaf ? t->ws_leaf.ptr : t->ws_stitch.ptr;
@@ -502,6 +516,9 @@ void tk_tree_destroy(tk_tree* t) {
                     &t->plan};
   for (DevBuf* b : bufs) dfree(*b);
   for (int n = 0; n < TK_MAXP; ++n) dfree(t->fac_pool[n]);
+  if (t->side) cudaStreamDestroy(t->side);
+  if (t->ev_plan) cudaEventDestroy(t->ev_plan);
+  if (t->ev_heavy) cudaEventDestroy(t->ev_heavy);
   if (t->own_stream && t->stream) cudaStreamDestroy(t->stream);
   delete t;
 }
@@ -704,16 +721,50 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
   qb.info = d_info;
   qb.order = nullptr;
   for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
-  if (n > 1) {  // longest-first schedule: heavy queries must not start last
-    rc = dalloc(t->plan, sizeof(int) * (size_t)n);
+  if (n > 1) {
+    // longest-first order; the heavy head of it runs on the side stream in
+    // big CTAs while the rest runs here, and this stream waits for both
+    if (!t->side) {
+      int lo = 0, hi = 0;
+      cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      if (cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+          cudaEventCreateWithFlags(&t->ev_plan, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&t->ev_heavy, cudaEventDisableTiming) != cudaSuccess)
+        return TK_ERR_CUDA;
+    }
+    const int hgrid = std::min(n, t->sm_count);
+    const int64_t per = stitch_ws_bound(t, max_hits(t, t->nbcap));
+    rc = dalloc(t->plan, sizeof(int) * ((size_t)n + 4));
+    if (rc == TK_OK) rc = ensure_ws_stitch(t, grid + hgrid);
     if (rc) return rc;
-    rc = tk_launch_plan(make_view(t), n, d_ranges, (int*)t->plan.ptr, t->stream);
+    int* split = (int*)t->plan.ptr;
+    int* order = split + 4;
+    rc = tk_launch_plan(make_view(t), n, d_ranges, heavy_hits(t), split, order, t->stream);
     t->launches += 1;
     if (rc) return rc;
-    qb.order = (const int*)t->plan.ptr;
+    qb.order = order;
+    qb.split = split;
+    TkWorkspace wl = ws_view(t, false), wh = ws_view(t, false);
+    wh.base = (char*)t->ws_stitch.ptr + (size_t)grid * per * t->es;
+    wh.warps = heavy_warps(t);
+    wh.smem_arena = heavy_arena(t);
+    wh.counter = (unsigned*)((char*)t->status.ptr + 20);
+    rc = cuda_ok(cudaEventRecord(t->ev_plan, t->stream));
+    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->side, t->ev_plan, 0));
+    if (rc) return rc;
+    qb.part = 1;
+    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wh, hgrid, t->side);
+    t->launches += 1;
+    if (rc == TK_OK) rc = cuda_ok(cudaEventRecord(t->ev_heavy, t->side));
+    if (rc) return rc;
+    qb.part = 2;
+    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wl, grid, t->stream);
+    t->launches += 1;
+    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->stream, t->ev_heavy, 0));
+  } else {
+    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
+    t->launches += 1;
   }
-  rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
-  t->launches += 1;
   if (rc) return rc;
   if (io == TK_IO_HOST) {
     rc = cuda_ok(cudaMemcpyAsync(out, d_out, (size_t)offsets[n] * t->es, cudaMemcpyDeviceToHost, t->stream));

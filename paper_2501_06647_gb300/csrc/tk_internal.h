@@ -61,6 +61,8 @@ struct TkQueryBatch {
   void* out;               // device
   tk_query_info* info;     // device, n (may be null)
   const int* order;        // device, n: processing order (may be null: index order)
+  const int* split;        // device: number of leading entries of `order` in part 1
+  int part;                // 0: jobs [0, n); 1: jobs [0, *split); 2: jobs [*split, n)
   int rq[TK_MAXP];         // requested ranks
 };
 
@@ -72,7 +74,9 @@ int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int 
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
 int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
-int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int* order, cudaStream_t stream);
+// order[0..n) longest first; *split = how many queries have >= heavy_hits hits.
+int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int heavy_hits, int* split, int* order,
+                   cudaStream_t stream);
 int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap,
                      int* counts, cudaStream_t stream);
 

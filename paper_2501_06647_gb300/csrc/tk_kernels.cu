@@ -71,6 +71,7 @@ template <class S> struct WarpSm {
   int flag;
   int job;
   int nsw;
+  S thr;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -395,6 +396,7 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
   js.flag = &sm.flag;
   js.red = sm.red;
   js.nsw = &sm.nsw;
+  js.thr = &sm.thr;
   S* T = cx.T;
   const int maxsw = sizeof(S) == 8 ? 24 : 16;
   bool have_v[TK_MAXP];
@@ -402,13 +404,14 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
   int sweeps = 0;
   // eigenvectors of the order-nsz matrix in A, warm-started from the mode's previous basis
   auto eig = [&](int mode_n, int nsz) {
+    const int rkeep = cx.ro[mode_n];
     S* Vs = cx.Vs[mode_n];
     const bool warm = have_v[mode_n];
     if (warm) {
       for (int i = lane; i < nsz * nsz; i += nt) V[i] = Vs[i];
       G::sync();
     }
-    sweeps += jacobi_eig<G, S>(nsz, A, V, T, warm, wv, js, maxsw);
+    sweeps += jacobi_eig<G, S>(nsz, rkeep, A, V, T, warm, wv, js, maxsw);
     for (int i = lane; i < nsz * nsz; i += nt) Vs[i] = V[i];
     G::sync();
     have_v[mode_n] = true;
@@ -667,8 +670,8 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
 // takes the next job index from the launch's queue counter (zeroed by the
 // host before the launch) and runs it.
 template <class S, class G>
-__global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int level, int64_t k0, int njobs,
-                                                  TkQueryBatch qb, TkWorkspace wsd) {
+__global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, int level, int64_t k0,
+                                                      int njobs, TkQueryBatch qb, TkWorkspace wsd) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int grp = G::size() == 32 ? (int)(threadIdx.x >> 5) : 0;
   const int ngrp = G::size() == 32 ? (int)(blockDim.x >> 5) : 1;
@@ -678,12 +681,15 @@ __global__ void __launch_bounds__(TK_NT) k_stitch(TkTreeView tv, int mode, int l
   WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(gsm);
   const int64_t gid = (int64_t)blockIdx.x * ngrp + grp;
   S* ws = reinterpret_cast<S*>(wsd.base) + gid * wsd.per_cta;
+  int job_lo = 0, job_hi = njobs;
+  if (qb.part == 1) job_hi = *qb.split;
+  if (qb.part == 2) job_lo = *qb.split;
   while (true) {
-    if (tid == 0) sm.job = (int)atomicAdd(wsd.counter, 1u);
+    if (tid == 0) sm.job = job_lo + (int)atomicAdd(wsd.counter, 1u);
     G::sync();
     const int job = sm.job;
     G::sync();
-    if (job >= njobs) break;
+    if (job >= job_hi) break;
     if (mode == TK_JOB_QUERY) {
       const int q = qb.order ? qb.order[job] : job;
       const int64_t ts = qb.ranges[2 * q], te = qb.ranges[2 * q + 1];
@@ -738,6 +744,7 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
     S sc[4];
     int flag;
     int nsw;
+    S thr;
     int rl[TK_MAXP];
     int64_t off_U[TK_MAXP], off_Vs[TK_MAXP], off_b0, off_b1, off_G, off_T, off_A, off_V, off_w, off_cs, off_pq;
     int err, eig_in_smem;
@@ -834,6 +841,7 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
     js.flag = &sm.flag;
     js.red = sm.red;
     js.nsw = &sm.nsw;
+    js.thr = &sm.thr;
     S* T = ws + sm.off_T;
     bool have_v[TK_MAXP];
     for (int n = 0; n < TK_MAXP; ++n) have_v[n] = false;
@@ -844,7 +852,7 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
         for (int i = tid; i < nsz * nsz; i += blockDim.x) V[i] = Vs[i];
         __syncthreads();
       }
-      jacobi_eig<BG, S>(nsz, A, V, T, warm, ew, js, maxsw);
+      jacobi_eig<BG, S>(nsz, rl[mode_n], A, V, T, warm, ew, js, maxsw);
       for (int i = tid; i < nsz * nsz; i += blockDim.x) Vs[i] = V[i];
       __syncthreads();
       have_v[mode_n] = true;
@@ -933,7 +941,7 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
 // decreasing hit-set size (a proxy of their cost: the eigenproblem orders
 // grow with it), by a counting sort in one CTA.  Ties keep no particular order;
 // the order only schedules work (every query writes its own outputs).
-__global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, int* order) {
+__global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, int heavy_hits, int* split, int* order) {
   constexpr int NB = TK_MAXH + 1;
   __shared__ int hist[NB];
   __shared__ int base[NB];
@@ -945,11 +953,13 @@ __global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, int* order) 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int acc = 0;
+    int acc = 0, heavy = 0;
     for (int b = NB - 1; b >= 0; --b) {
       base[b] = acc;
       acc += hist[b];
+      if (b >= heavy_hits) heavy += hist[b];
     }
+    *split = heavy;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -1029,6 +1039,7 @@ int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t blo
 static int launch_stitch(int dtype, const TkTreeView& tv, int mode, int level, int64_t k0, int njobs,
                          const TkQueryBatch& qb, const TkWorkspace& ws, int grid, cudaStream_t stream) {
   const size_t smem = tk_stitch_smem_bytes(dtype, ws.smem_arena);
+  if (ws.warps * 32 > 2 * TK_NT) return TK_ERR_ARG;
   if (cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), stream) != cudaSuccess) return TK_ERR_CUDA;
   if (dtype == TK_F64) {
     if (set_smem_attr(stitch_fn<double>(), smem)) return TK_ERR_CUDA;
@@ -1053,9 +1064,10 @@ int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, con
   return launch_stitch(dtype, tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws, grid, stream);
 }
 
-int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int* order, cudaStream_t stream) {
+int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int heavy_hits, int* split, int* order,
+                   cudaStream_t stream) {
   if (n <= 0) return TK_OK;
-  k_plan<<<1, 1024, 0, stream>>>(tv, n, ranges, order);
+  k_plan<<<1, 1024, 0, stream>>>(tv, n, ranges, heavy_hits, split, order);
   return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
 
