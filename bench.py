@@ -13,6 +13,7 @@ workload.  Multi-GPU runs are replicas (every rank holds the tree and answers
 its own copy of the query batch; no collective on the data path).
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -242,6 +243,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp32_plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="length of the serving run (appends at 1 kHz; 15.36 s covers T 1024 -> 16384)")
     args = ap.parse_args()
     w = synth.WORKLOADS[args.workload]
     if args.warmup < 3:
@@ -353,7 +356,6 @@ def main():
     e2e_value = world * n_q * e2e_steps / e2e_s
 
     # ---- roofline of the dominant kernel (the batched stitch launch) -------------
-    info = (tk.TkQueryInfo * n_q)()
     out_chk, _, info = tree.query_batch_host(Q, offsets, None, with_info=True)
     flops = 0.0
     for i, (ts, te) in enumerate(Q):
@@ -385,6 +387,13 @@ def main():
         "clocks": clk.summary(),
     }
 
+    del out_d, flush
+    torch.cuda.empty_cache()
+
+    # ---- serving: interleaved appends and Poisson queries through the server -----
+    if args.serve_seconds > 0:
+        line["serving"] = serving_section(tk, torch, dev, local, args.serve_seconds)
+
     # ---- FP64 oracle on the host cores: cpu_baseline + matched-error check -------
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -392,12 +401,103 @@ def main():
         except Exception as exc:  # report, do not lose the GPU measurement
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                     "sample": None, "error": f"{type(exc).__name__}: {exc}"}
+    tree.close()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
-    tree.close()
     return 0
+
+
+def serving_section(tk, torch, dev, local, seconds):
+    """Continuous batching under load: a 4-way 64x64x32 stream (ranks 8, leaf
+    16, FP32) grows from T0 = 1024 by single-slice appends at 1 kHz while range
+    queries of log-uniform length (16..T as of arrival) arrive as a Poisson
+    process at 5k/s; all go through the native server.  Latency is submit to
+    result in host memory (host clock).  Then a burst of 4096 queries at the
+    final T measures the server's saturated throughput."""
+    w = synth.WORKLOADS["serving_4way"]
+    T0 = w["T0"]
+    n_app = int(round(seconds * w["append_hz"]))
+    T_end = T0 + n_app
+    X = synth.piecewise_tucker_regimes(T_end, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local)
+    tree.build(torch.from_numpy(X[:T0]).to(dev))
+    tree.sync()
+    # arrival schedule: appends every 1 ms, queries at exponential gaps
+    rng = np.random.Generator(np.random.PCG64(w["qseed"]))
+    n_q = int(seconds * w["query_hz"] * 1.5) + 16
+    qt = np.cumsum(rng.exponential(1.0 / w["query_hz"], n_q))
+    qt = qt[qt < seconds]
+    at = (np.arange(n_app) + 0.5) / w["append_hz"]
+    events = sorted([(t, 1, i) for i, t in enumerate(at)] + [(t, 0, i) for i, t in enumerate(qt)])
+    u = rng.uniform(size=(len(qt), 2))
+    dims, rk = w["dims"], w["ranks"]
+    fixed = int(np.prod(rk)) + sum(d * r for d, r in zip(dims, rk[1:]))
+    K = 512
+    ring = np.empty((K, fixed + T_end * rk[0]), dtype=np.float32)
+    ring_ticket = [0] * K
+    lib_ = tk.lib()
+    srv = tk.Server(tree, max_batch=1024, max_batch_out_elems=64 << 20)
+    tkt = ctypes.c_uint64()
+    T_sub, qi, lens = T0, 0, []
+    t0 = time.perf_counter()
+    for t_ev, kind, i in events:
+        while time.perf_counter() - t0 < t_ev:
+            pass
+        if kind == 1:
+            srv.submit_append(X[T_sub])
+            T_sub += 1
+            continue
+        Lq = int(round(np.exp(np.log(w["lo"]) + u[i, 0] * (np.log(T_sub) - np.log(w["lo"])))))
+        Lq = max(1, min(Lq, T_sub))
+        ts = min(int(u[i, 1] * (T_sub - Lq + 1)), T_sub - Lq)
+        slot = qi % K
+        if ring_ticket[slot]:
+            lib_.tk_server_wait(srv.h, ring_ticket[slot], -1.0)
+        rc = lib_.tk_server_submit_query(srv.h, ts, ts + Lq, None, ring[slot].ctypes.data, None, ctypes.byref(tkt))
+        if rc != 0:
+            raise tk.TuckerError(rc, "tk_server_submit_query")
+        ring_ticket[slot] = tkt.value
+        lens.append(Lq)
+        qi += 1
+    srv.drain()
+    st_load = srv.stats()
+    for slot in range(K):
+        if ring_ticket[slot]:
+            lib_.tk_server_wait(srv.h, ring_ticket[slot], -1.0)
+            ring_ticket[slot] = 0
+    srv.close()
+    # saturated burst at the final T (a fresh server, so that its counters start at zero)
+    srv = tk.Server(tree, max_batch=1024, max_batch_out_elems=64 << 20)
+    nb = 4096
+    qb = synth.query_ranges(T_end, nb, w["qseed"] + 1, "loguniform", w["lo"], T_end)
+    sizes = [fixed + int(te - ts) * rk[0] for ts, te in qb]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    flat = np.empty(int(offs[-1]), dtype=np.float32)
+    base = flat.ctypes.data
+    for j, (ts, te) in enumerate(qb):
+        rc = lib_.tk_server_submit_query(srv.h, int(ts), int(te), None, base + 4 * int(offs[j]), None,
+                                         ctypes.byref(tkt))
+        if rc != 0:
+            raise tk.TuckerError(rc, "tk_server_submit_query")
+    srv.drain()
+    st_burst = srv.stats()
+    srv.close()
+    tree.close()
+    return {
+        "workload": f"4-way {dims[0]}x{dims[1]}x{dims[2]}xT, T {T0}->{T_end} by appends at "
+                    f"{w['append_hz']:.0f} Hz, Poisson queries at {w['query_hz']:.0f}/s of log-uniform length "
+                    f"{w['lo']}..T, ranks {rk}, leaf {w['B']}, FP32, tol 0.01",
+        "seconds": seconds, "queries": int(st_load["queries_done"]), "appends": int(st_load["appends_done"]),
+        "offered_qps": len(qt) / seconds, "served_qps": st_load["queries_done"] / st_load["elapsed_s"],
+        "latency_ms": {"p50": st_load["latency_p50_ms"], "p99": st_load["latency_p99_ms"],
+                       "max": st_load["latency_max_ms"], "clock": "host, submit to result in host memory"},
+        "mean_batch": st_load["mean_batch"], "mean_query_len": float(np.mean(lens)) if lens else 0.0,
+        "burst": {"queries": nb, "qps": st_burst["queries_done"] / st_burst["elapsed_s"],
+                  "mean_batch": st_burst["mean_batch"], "latency_p50_ms": st_burst["latency_p50_ms"],
+                  "latency_p99_ms": st_burst["latency_p99_ms"], "T": T_end},
+    }
 
 
 def cpu_section(line, w, X, Q, offsets, tree, out_chk, info, n_q):

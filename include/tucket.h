@@ -46,7 +46,8 @@ typedef enum tk_status {
   TK_ERR_CUDA = -5,        /* a CUDA runtime call failed */
   TK_ERR_STATE = -6,       /* call not valid in the tree's current state */
   TK_ERR_WORKSPACE = -7,   /* device job exceeded its workspace (reported by tk_sync) */
-  TK_ERR_TOO_BIG = -8      /* request exceeds a fixed limit of the engine */
+  TK_ERR_TOO_BIG = -8,     /* request exceeds a fixed limit of the engine */
+  TK_ERR_TIMEOUT = -9      /* a wait ran out of time */
 } tk_status;
 
 typedef enum tk_dtype { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
@@ -156,6 +157,51 @@ int tk_sync(tk_tree* t);
 int64_t tk_launch_count(const tk_tree* t);
 
 const char* tk_strerror(int code);
+
+/* Copy of the configuration the tree was created with. */
+int tk_tree_get_config(const tk_tree* t, tk_config* out);
+
+/* ---- Serving: continuous batching of queries and appends ---------------
+ *
+ * A server owns a worker thread that executes the requests submitted to it,
+ * from any host thread, in ticket (arrival) order: a range query sees every
+ * stream update submitted before it (Section 3's two operations, served
+ * concurrently).  Queries waiting at the head of the queue are admitted into
+ * one batched launch, up to max_batch queries and max_batch_out_elems output
+ * elements (the device memory a batch may hold); the next batch is enqueued
+ * while the current one runs, and appends are applied between batches.
+ * While a server exists, the tree must not be used directly. */
+typedef struct tk_server tk_server;
+typedef struct tk_server_config {
+  int32_t max_batch;               /* queries per batch (default 1024) */
+  int64_t max_batch_out_elems;     /* output elements per batch (default 16 Mi) */
+} tk_server_config;
+typedef struct tk_server_stats {
+  int64_t queries_done, appends_done, batches;
+  double mean_batch;               /* queries per batch */
+  double latency_p50_ms, latency_p99_ms, latency_max_ms;  /* queries: submit to completion */
+  double elapsed_s;                /* first submit to last completion */
+} tk_server_stats;
+
+/* cfg may be NULL (defaults). */
+int tk_server_create(tk_tree* t, const tk_server_config* cfg, tk_server** out);
+/* Queue a range query [t_s, t_e) (checked against T including queued
+ * appends); the packed output (tk_query_output_elems layout) is written to
+ * out_host and the report to info_host (may be NULL) on completion. */
+int tk_server_submit_query(tk_server* s, int64_t t_s, int64_t t_e, const int32_t* ranks, void* out_host,
+                           tk_query_info* info_host, uint64_t* ticket);
+/* Queue a stream update; the slice (host memory) is copied at submission. */
+int tk_server_submit_append(tk_server* s, const void* slice_host, uint64_t* ticket);
+/* Wait for one request (timeout_s < 0: no limit); returns its status, or
+ * TK_ERR_TIMEOUT.  A ticket's status can be collected once: an unknown or
+ * already collected ticket gives TK_ERR_ARG.  Statuses that are never
+ * collected are kept until the server is destroyed. */
+int tk_server_wait(tk_server* s, uint64_t ticket, double timeout_s);
+/* Wait until every submitted request has completed. */
+int tk_server_drain(tk_server* s, double timeout_s);
+int tk_server_get_stats(tk_server* s, tk_server_stats* out);
+/* Finish the queued requests, stop the worker and free the server. */
+void tk_server_destroy(tk_server* s);
 
 /* ---- Allocation-free range queries (no counterpart in the paper) --------
  *

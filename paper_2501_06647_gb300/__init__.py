@@ -22,6 +22,7 @@ _ERR = {
     -1: "invalid argument", -2: "time range outside [0, T) or empty", -3: "query rank out of bounds",
     -4: "device allocation failed", -5: "CUDA runtime error", -6: "invalid tree state",
     -7: "device job exceeded its workspace", -8: "request exceeds an engine limit",
+    -9: "a wait ran out of time",
 }
 
 
@@ -43,6 +44,17 @@ class TkQueryInfo(ctypes.Structure):
     _fields_ = [("ranks", ctypes.c_int32 * MAX_MODES), ("iters", ctypes.c_int32),
                 ("n_hits", ctypes.c_int32), ("fit_err", ctypes.c_double), ("eig_sweeps", ctypes.c_int32),
                 ("eig_max_order", ctypes.c_int32), ("device_cycles", ctypes.c_int64)]
+
+
+class TkServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("max_batch_out_elems", ctypes.c_int64)]
+
+
+class TkServerStats(ctypes.Structure):
+    _fields_ = [("queries_done", ctypes.c_int64), ("appends_done", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double),
+                ("elapsed_s", ctypes.c_double)]
 
 
 # Every symbol the header declares, with its ctypes signature.
@@ -71,6 +83,16 @@ _SIGS = {
     "tk_range_query_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p]),
+    "tk_tree_get_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TkConfig)]),
+    "tk_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TkServerConfig),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "tk_server_submit_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "tk_server_submit_append": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "tk_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
+    "tk_server_drain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "tk_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TkServerStats)]),
+    "tk_server_destroy": (None, [ctypes.c_void_p]),
 }
 
 _lib_handle = None
@@ -294,3 +316,71 @@ class Tree:
         G, U = self.unpack(out, hi - lo)
         r = list(rk[: self.p])
         return G[tuple(slice(0, x) for x in r)], [u[:, :x] for u, x in zip(U, r)], r
+
+
+class Server:
+    """Continuous-batching server over one Tree (native worker thread).
+
+    Queries and stream updates submitted from any thread run in submission
+    order; queries waiting together are batched into one launch.  The tree
+    must not be used directly while the server exists.
+    """
+
+    def __init__(self, tree, max_batch=1024, max_batch_out_elems=16 << 20):
+        self.tree = tree
+        cfg = TkServerConfig(int(max_batch), int(max_batch_out_elems))
+        h = ctypes.c_void_p()
+        _check(lib().tk_server_create(tree.h, ctypes.byref(cfg), ctypes.byref(h)), "tk_server_create")
+        self.h = h
+        self._live = {}  # ticket -> host buffers the worker writes into
+
+    def submit_query(self, ts, te, ranks=None):
+        """Queue a range query; returns its ticket."""
+        rarr, rq = self.tree._ranks_arg(ranks)
+        L = int(te) - int(ts)
+        n = int(np.prod(rq)) + L * rq[0] + sum(d * r for d, r in zip(self.tree.dims, rq[1:]))
+        out = np.empty(max(n, 1), dtype=self.tree.np_dtype)
+        info = TkQueryInfo()
+        tk = ctypes.c_uint64()
+        _check(lib().tk_server_submit_query(self.h, int(ts), int(te), rarr, _ptr(out), ctypes.byref(info),
+                                            ctypes.byref(tk)), "tk_server_submit_query")
+        self._live[tk.value] = (out, info, L, rq)
+        return tk.value
+
+    def submit_append(self, X_T):
+        """Queue a stream update with one host slice; returns its ticket."""
+        X_T = np.ascontiguousarray(X_T, dtype=self.tree.np_dtype)
+        tk = ctypes.c_uint64()
+        _check(lib().tk_server_submit_append(self.h, _ptr(X_T), ctypes.byref(tk)), "tk_server_submit_append")
+        return tk.value
+
+    def wait(self, ticket, timeout=-1.0):
+        """Wait for a request: a query gives (G, U, info), an append None."""
+        _check(lib().tk_server_wait(self.h, int(ticket), float(timeout)), "tk_server_wait")
+        rec = self._live.pop(int(ticket), None)
+        if rec is None:
+            return None
+        out, info, L, rq = rec
+        G, U = self.tree.unpack(out, L, rq)
+        r = list(info.ranks[: self.tree.p])
+        return (G[tuple(slice(0, x) for x in r)], [u[:, :x] for u, x in zip(U, r)],
+                dict(ranks=r, iters=info.iters, n_hits=info.n_hits, fit_err=info.fit_err))
+
+    def drain(self, timeout=-1.0):
+        _check(lib().tk_server_drain(self.h, float(timeout)), "tk_server_drain")
+
+    def stats(self):
+        st = TkServerStats()
+        _check(lib().tk_server_get_stats(self.h, ctypes.byref(st)), "tk_server_get_stats")
+        return {k: getattr(st, k) for k, _ in TkServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tk_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

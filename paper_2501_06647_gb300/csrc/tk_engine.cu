@@ -423,6 +423,71 @@ int64_t out_elems(const tk_tree* t, int64_t L, const int* rq) {
   return c;
 }
 
+// One batch launch sequence (plan, heavy part on the side stream, light part)
+// with all pointers on the device.  Asynchronous on the tree's stream.
+int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_offsets, const int* rq, void* d_out,
+                 tk_query_info* d_info) {
+  int rc = TK_OK;
+  if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
+  const int grid = grid_for(t, false, n);
+  rc = ensure_ws_stitch(t, grid);
+  if (rc) return rc;
+  TkQueryBatch qb{};
+  qb.n = n;
+  qb.ranges = d_ranges;
+  qb.offsets = d_offsets;
+  qb.out = d_out;
+  qb.info = d_info;
+  qb.order = nullptr;
+  for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
+  if (n > 1) {
+    // longest-first order; the heavy head of it runs on the side stream in
+    // big CTAs while the rest runs here, and this stream waits for both
+    if (!t->side) {
+      int lo = 0, hi = 0;
+      cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      if (cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+          cudaEventCreateWithFlags(&t->ev_plan, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&t->ev_heavy, cudaEventDisableTiming) != cudaSuccess)
+        return TK_ERR_CUDA;
+    }
+    const int hgrid = std::min(n, t->sm_count);
+    const int64_t per = stitch_ws_bound(t, max_hits(t, t->nbcap));
+    rc = dalloc(t->plan, sizeof(int) * ((size_t)n + 4));
+    if (rc == TK_OK) rc = ensure_ws_stitch(t, grid + hgrid);
+    if (rc) return rc;
+    int* split = (int*)t->plan.ptr;
+    int* order = split + 4;
+    rc = tk_launch_plan(make_view(t), n, d_ranges, heavy_hits(t), split, order, t->stream);
+    t->launches += 1;
+    if (rc) return rc;
+    qb.order = order;
+    qb.split = split;
+    TkWorkspace wl = ws_view(t, false), wh = ws_view(t, false);
+    wh.base = (char*)t->ws_stitch.ptr + (size_t)grid * per * t->es;
+    wh.warps = heavy_warps(t);
+    wh.smem_arena = heavy_arena(t);
+    wh.counter = (unsigned*)((char*)t->status.ptr + 20);
+    rc = cuda_ok(cudaEventRecord(t->ev_plan, t->stream));
+    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->side, t->ev_plan, 0));
+    if (rc) return rc;
+    qb.part = 1;
+    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wh, hgrid, t->side);
+    t->launches += 1;
+    if (rc == TK_OK) rc = cuda_ok(cudaEventRecord(t->ev_heavy, t->side));
+    if (rc) return rc;
+    qb.part = 2;
+    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wl, grid, t->stream);
+    t->launches += 1;
+    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->stream, t->ev_heavy, 0));
+  } else {
+    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
+    t->launches += 1;
+  }
+  if (rc) return rc;
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -438,6 +503,7 @@ const char* tk_strerror(int code) {
     case TK_ERR_STATE: return "call not valid in the current tree state";
     case TK_ERR_WORKSPACE: return "device job exceeded its workspace or hit limit";
     case TK_ERR_TOO_BIG: return "request exceeds a fixed engine limit";
+    case TK_ERR_TIMEOUT: return "a wait ran out of time";
     default: return "unknown error";
   }
 }
@@ -524,6 +590,12 @@ void tk_tree_destroy(tk_tree* t) {
 }
 
 int64_t tk_timespan(const tk_tree* t) { return t ? t->T : -1; }
+
+int tk_tree_get_config(const tk_tree* t, tk_config* out) {
+  if (!t || !out) return TK_ERR_ARG;
+  *out = t->cfg;
+  return TK_OK;
+}
 int64_t tk_launch_count(const tk_tree* t) { return t ? t->launches : -1; }
 
 int64_t tk_arena_bytes(const tk_tree* t) {
@@ -709,62 +781,7 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
     if (rc) return rc;
     d_info = (tk_query_info*)t->stage_info.ptr;
   }
-  if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
-  const int grid = grid_for(t, false, n);
-  rc = ensure_ws_stitch(t, grid);
-  if (rc) return rc;
-  TkQueryBatch qb{};
-  qb.n = n;
-  qb.ranges = d_ranges;
-  qb.offsets = d_offsets;
-  qb.out = d_out;
-  qb.info = d_info;
-  qb.order = nullptr;
-  for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
-  if (n > 1) {
-    // longest-first order; the heavy head of it runs on the side stream in
-    // big CTAs while the rest runs here, and this stream waits for both
-    if (!t->side) {
-      int lo = 0, hi = 0;
-      cudaDeviceGetStreamPriorityRange(&lo, &hi);
-      if (cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
-          cudaEventCreateWithFlags(&t->ev_plan, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&t->ev_heavy, cudaEventDisableTiming) != cudaSuccess)
-        return TK_ERR_CUDA;
-    }
-    const int hgrid = std::min(n, t->sm_count);
-    const int64_t per = stitch_ws_bound(t, max_hits(t, t->nbcap));
-    rc = dalloc(t->plan, sizeof(int) * ((size_t)n + 4));
-    if (rc == TK_OK) rc = ensure_ws_stitch(t, grid + hgrid);
-    if (rc) return rc;
-    int* split = (int*)t->plan.ptr;
-    int* order = split + 4;
-    rc = tk_launch_plan(make_view(t), n, d_ranges, heavy_hits(t), split, order, t->stream);
-    t->launches += 1;
-    if (rc) return rc;
-    qb.order = order;
-    qb.split = split;
-    TkWorkspace wl = ws_view(t, false), wh = ws_view(t, false);
-    wh.base = (char*)t->ws_stitch.ptr + (size_t)grid * per * t->es;
-    wh.warps = heavy_warps(t);
-    wh.smem_arena = heavy_arena(t);
-    wh.counter = (unsigned*)((char*)t->status.ptr + 20);
-    rc = cuda_ok(cudaEventRecord(t->ev_plan, t->stream));
-    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->side, t->ev_plan, 0));
-    if (rc) return rc;
-    qb.part = 1;
-    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wh, hgrid, t->side);
-    t->launches += 1;
-    if (rc == TK_OK) rc = cuda_ok(cudaEventRecord(t->ev_heavy, t->side));
-    if (rc) return rc;
-    qb.part = 2;
-    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wl, grid, t->stream);
-    t->launches += 1;
-    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->stream, t->ev_heavy, 0));
-  } else {
-    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
-    t->launches += 1;
-  }
+  rc = launch_batch(t, n, d_ranges, d_offsets, rq, d_out, d_info);
   if (rc) return rc;
   if (io == TK_IO_HOST) {
     rc = cuda_ok(cudaMemcpyAsync(out, d_out, (size_t)offsets[n] * t->es, cudaMemcpyDeviceToHost, t->stream));
@@ -780,6 +797,30 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
   }
   return TK_OK;
 }
+
+}  // extern "C"
+
+// Batched queries with every pointer on the device, reports included;
+// asynchronous.  Used by the serving runtime (tk_server.cu).
+int tk_query_batch_device(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_offsets,
+                          const int32_t* ranks, void* d_out, tk_query_info* d_info) {
+  if (!t || n < 0) return TK_ERR_ARG;
+  if (n == 0) return TK_OK;
+  DeviceGuard g(t->dev);
+  int rq[TK_MAXP];
+  int rc = check_ranks(t, ranks, rq);
+  if (rc) return rc;
+  if (t->T == 0) return TK_ERR_RANGE;
+  rc = ensure_tail(t);
+  if (rc) return rc;
+  return launch_batch(t, n, d_ranges, d_offsets, rq, d_out, d_info);
+}
+
+cudaStream_t tk_tree_stream(const tk_tree* t) { return t->stream; }
+int tk_tree_device(const tk_tree* t) { return t->dev; }
+size_t tk_tree_elem_size(const tk_tree* t) { return t->es; }
+
+extern "C" {
 
 int tk_range_query(tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks, void* out, tk_query_info* info,
                    int io) {

@@ -14,6 +14,12 @@ has unit RMS per entry (``unit_signal``) unless ``literal_scale`` is set.
 Finally i.i.d. N(0, sigma^2) noise is added, slab by slab, from the same
 generator.
 
+Streaming series (``piecewise_tucker_regimes``): the same recipe, but each
+regime draws from its own generator, spawned from ``SeedSequence(seed)``, and
+adds its own noise; regimes are generated in parallel threads straight into a
+float32 array.  It stands in for the long 4-way streams of the serving runs,
+where one generator over the whole series would be too slow.
+
 Query ranges: "uniform" draws two distinct integers of {0..T}, sorted, read
 as the half-open range [a, b); "loguniform" draws L = round(exp(U[ln lo,
 ln hi])) and t_s uniformly from {0..T-L}.
@@ -54,6 +60,41 @@ def piecewise_tucker(T, dims, ranks, regime, sigma, seed, literal_scale=False, d
     return X.astype(dtype, copy=False)
 
 
+def _regime(X, start, l, dims, ranks, sigma, ss, literal_scale):
+    rng = np.random.Generator(np.random.PCG64(ss))
+    p = len(ranks)
+    letters = string.ascii_lowercase
+    core_idx, out_idx = letters[:p], letters[13:13 + p]
+    rr = [min(ranks[0], l)] + [min(r, d) for r, d in zip(ranks[1:], dims)]
+    core = rng.standard_normal(tuple(rr))
+    if not literal_scale:
+        core *= np.sqrt(l * np.prod(dims) / np.prod(rr))
+    facs = [_orthonormal(rng, l, rr[0])] + [_orthonormal(rng, d, r) for d, r in zip(dims, rr[1:])]
+    spec = core_idx + "," + ",".join(out_idx[n] + core_idx[n] for n in range(p)) + "->" + out_idx
+    for i in range(0, l, 64):  # slab by slab, to bound the float64 temporaries
+        j = min(l, i + 64)
+        sig = np.einsum(spec, core, facs[0][i:j], *facs[1:], optimize=True)
+        X[start + i:start + j] = sig + sigma * rng.standard_normal(sig.shape)
+
+
+def piecewise_tucker_regimes(T, dims, ranks, regime, sigma, seed, literal_scale=False, threads=8):
+    """Seeded piecewise-Tucker series in float32, one generator per regime."""
+    from concurrent.futures import ThreadPoolExecutor
+    dims = tuple(int(d) for d in dims)
+    ranks = tuple(int(r) for r in ranks)
+    assert len(dims) == len(ranks) - 1
+    T, regime = int(T), int(regime)
+    X = np.empty((T,) + dims, dtype=np.float32)
+    starts = list(range(0, T, regime))
+    seeds = np.random.SeedSequence(int(seed)).spawn(len(starts))
+    with ThreadPoolExecutor(max_workers=max(1, int(threads))) as ex:
+        futs = [ex.submit(_regime, X, s0, min(regime, T - s0), dims, ranks, sigma, ss, literal_scale)
+                for s0, ss in zip(starts, seeds)]
+        for f in futs:
+            f.result()
+    return X
+
+
 def query_ranges(T, n, seed, kind="uniform", lo=16, hi=None):
     """n seeded query ranges [t_s, t_e) over a series of length T."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))
@@ -82,4 +123,8 @@ WORKLOADS = {
     "fp32_plain": dict(T=4096, dims=(100, 100), ranks=(10, 10, 10), regime=512, sigma=0.05, B=16,
                        n_queries=1000, kind="loguniform", lo=16, hi=4096, seed=1002, qseed=2002,
                        dtype="f32"),
+    # 4-way stream grown by single-slice appends at append_hz while Poisson
+    # range queries of log-uniform length (16..T) arrive at query_hz.
+    "serving_4way": dict(T0=1024, T_end=16384, dims=(64, 64, 32), ranks=(8, 8, 8, 8), regime=512, sigma=0.05,
+                         B=16, append_hz=1000.0, query_hz=5000.0, lo=16, seed=1004, qseed=2004, dtype="f32"),
 }
