@@ -84,7 +84,9 @@ typedef struct tk_query_info {
   double fit_err;                   /* sqrt(1 - ||G||^2 / ||Y~||^2) of the stitched tensor */
   int32_t eig_sweeps;               /* Jacobi sweeps summed over the query's eigenproblems */
   int32_t eig_max_order;            /* largest eigenproblem order of the query */
-  int64_t device_cycles;            /* SM clock cycles the query's warp spent on it */
+  int64_t device_cycles;            /* SM clock cycles the query's job group spent on it */
+  int64_t eig_cycles;               /* of which in the eigensolver (Jacobi) */
+  int64_t qr_cycles;                /* of which in Householder QR (partial hits and Phi_n) */
 } tk_query_info;
 
 typedef struct tk_tree tk_tree;

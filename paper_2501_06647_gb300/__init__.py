@@ -43,7 +43,8 @@ class TkHit(ctypes.Structure):
 class TkQueryInfo(ctypes.Structure):
     _fields_ = [("ranks", ctypes.c_int32 * MAX_MODES), ("iters", ctypes.c_int32),
                 ("n_hits", ctypes.c_int32), ("fit_err", ctypes.c_double), ("eig_sweeps", ctypes.c_int32),
-                ("eig_max_order", ctypes.c_int32), ("device_cycles", ctypes.c_int64)]
+                ("eig_max_order", ctypes.c_int32), ("device_cycles", ctypes.c_int64),
+                ("eig_cycles", ctypes.c_int64), ("qr_cycles", ctypes.c_int64)]
 
 
 class TkServerConfig(ctypes.Structure):
@@ -257,7 +258,8 @@ class Tree:
         U = [u[:, :x] for u, x in zip(U, r)]
         return G, U, dict(ranks=r, iters=info.iters, n_hits=info.n_hits, fit_err=info.fit_err,
                           eig_sweeps=info.eig_sweeps, eig_max_order=info.eig_max_order,
-                          device_cycles=info.device_cycles)
+                          device_cycles=info.device_cycles, eig_cycles=info.eig_cycles,
+                          qr_cycles=info.qr_cycles)
 
     def layout(self, ranges, ranks=None):
         ranges = np.ascontiguousarray(ranges, dtype=np.int64).reshape(-1, 2)

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtucket.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tk_kernels.cu", "tk_engine.cu", "tk_server.cu"]
+SOURCES = ["tk_kernels.cu", "tk_leaf.cu", "tk_engine.cu", "tk_server.cu"]
 
 
 def nvcc_path():

@@ -10,6 +10,8 @@
 
 namespace tk {
 
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
 template <class S> struct Eps;
 template <> struct Eps<double> { static __device__ __forceinline__ double v() { return 2.220446049250313e-16; } };
 template <> struct Eps<float> { static __device__ __forceinline__ float v() { return 1.1920929e-7f; } };

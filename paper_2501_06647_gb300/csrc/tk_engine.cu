@@ -265,20 +265,69 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   return tot + 256;
 }
 
-int64_t leaf_ws_bound(const tk_tree* t) {
+// Workspace of one leaf cluster (see TkLeafLayout), with every rank at its
+// build value and the block at its full B slices: bounds for any block.
+TkLeafLayout leaf_layout(const tk_tree* t, int nsm, int64_t* per_cluster) {
+  TkLeafLayout ly{};
   const int p = t->p;
-  const int B = t->cfg.leaf_slices;
-  int64_t tot = 0, xel = B, neig = B, gel = 1;
-  tot += round32((int64_t)B * t->cfg.ranks[0]) + round32((int64_t)B * B);
-  for (int n = 1; n < p; ++n) {
-    tot += round32(t->cfg.dims[n] * t->cfg.ranks[n]) + round32(t->cfg.dims[n] * t->cfg.dims[n]);
-    xel *= t->cfg.dims[n];
-    neig = std::max<int64_t>(neig, t->cfg.dims[n]);
+  const int CL = TK_LEAF_CL;
+  int64_t xd[TK_MAXP], r[TK_MAXP];
+  xd[0] = t->cfg.leaf_slices;
+  for (int n = 1; n < p; ++n) xd[n] = t->cfg.dims[n];
+  for (int n = 0; n < p; ++n) r[n] = std::min<int64_t>(t->cfg.ranks[n], xd[n]);
+  int64_t N = 1, rprod = 1, neig = 0;
+  for (int n = 0; n < p; ++n) {
+    N *= xd[n];
+    rprod *= r[n];
+    neig = std::max(neig, xd[n]);
   }
-  for (int n = 0; n < p; ++n) gel *= t->cfg.ranks[n];
-  tot += 2 * round32(xel) + round32(gel);
-  tot += 3 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
-  return tot + 256;
+  int64_t cur = 0;
+  auto take = [&](int64_t nel) {
+    const int64_t o = cur;
+    cur += round32(nel);
+    return o;
+  };
+  int64_t ymax = 0;
+  for (int n = 0; n < p; ++n) {
+    ly.U[n] = take(xd[n] * r[n]);
+    ly.Vs[n] = take(xd[n] * xd[n]);
+    ly.part[n] = n > 0 ? take(CL * xd[n] * xd[n]) : 0;
+    ymax = std::max(ymax, xd[n] * (rprod / r[n]));
+  }
+  ly.norm = take(CL);
+  ly.flag = take(1);
+  ly.Y = take(ymax);
+  ly.G = take(rprod);
+  ly.cta = cur;
+  // per CTA: the gathered slab of mode n (n >= 1) and the chain buffers, whose
+  // largest content is the slab after its first contraction (mode p, or p-1
+  // when n is the last mode): every later contraction shrinks it
+  int64_t slab = 0, chain = 0;
+  for (int n = 0; n < p; ++n) {
+    const int64_t sl = (xd[n] + CL - 1) / CL * (N / xd[n]);
+    if (n > 0) slab = std::max(slab, sl);
+    const int m0 = n == p - 1 ? p - 2 : p - 1;
+    chain = std::max(chain, sl / xd[m0] * r[m0]);
+  }
+  cur = 0;
+  ly.slab = take(slab);
+  ly.b0 = take(chain);
+  ly.b1 = take(chain);
+  ly.T = take(neig * neig);
+  ly.nsm = nsm;
+  ly.neig = (int)neig;
+  ly.half = neig / 2 + 2;
+  ly.eig_in_smem = neig <= nsm;
+  if (!ly.eig_in_smem) {
+    ly.A = take(neig * neig);
+    ly.V = take(neig * neig);
+    ly.w = take(neig + 2);
+    ly.cs = take(2 * ly.half);
+    ly.pq = take(ly.half);
+  }
+  ly.cta_stride = cur + 32;
+  *per_cluster = ly.cta + CL * ly.cta_stride;
+  return ly;
 }
 
 int max_hits(const tk_tree* t, int64_t nbt) {
@@ -300,7 +349,7 @@ int stitch_warps(const tk_tree* t) { (void)t; return 8; }
 int pick_nsm_leaf(const tk_tree* t) {
   int need = t->cfg.leaf_slices;
   for (int n = 1; n < t->p; ++n) need = std::max<int>(need, (int)t->cfg.dims[n]);
-  const int cap = t->es == 8 ? 110 : 150;
+  const int cap = t->es == 8 ? 100 : 150;
   return std::max(2, std::min(need, cap));
 }
 
@@ -320,16 +369,18 @@ int ensure_ws_stitch(tk_tree* t, int want_ctas) {
   return TK_OK;
 }
 
-int ensure_ws_leaf(tk_tree* t, int want_ctas) {
-  const int64_t per = leaf_ws_bound(t);
+// Leaf workspace: one chunk per cluster of the grid.
+int ensure_ws_leaf(tk_tree* t, int want_clusters, TkLeafLayout* ly) {
   if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
-  int ctas = std::max(1, want_ctas);
-  if (per != t->ws_leaf_per_cta || ctas > t->ws_leaf_ctas) {
-    ctas = std::max(ctas, t->ws_leaf_ctas);
-    const int rc = dalloc(t->ws_leaf, (size_t)per * ctas * t->es);
+  int64_t per = 0;
+  *ly = leaf_layout(t, t->nsm_leaf, &per);
+  int n = std::max(1, want_clusters);
+  if (per != t->ws_leaf_per_cta || n > t->ws_leaf_ctas) {
+    n = std::max(n, t->ws_leaf_ctas);
+    const int rc = dalloc(t->ws_leaf, (size_t)per * n * t->es);
     if (rc) return rc;
     t->ws_leaf_per_cta = per;
-    t->ws_leaf_ctas = ctas;
+    t->ws_leaf_ctas = n;
   }
   return TK_OK;
 }
@@ -349,7 +400,7 @@ TkWorkspace ws_view(const tk_tree* t, bool leaf) {
   TkWorkspace w{};
   w.base = leaf ? t->ws_leaf.ptr : t->ws_stitch.ptr;
   w.per_cta = leaf ? t->ws_leaf_per_cta : t->ws_stitch_per_cta;
-  w.nsm = leaf ? t->nsm_leaf : 0;
+  w.nsm = 0;
   w.smem_arena = leaf ? 0 : (size_t)t->nsm_stitch;
   w.warps = stitch_warps(t);
   w.status = (int*)t->status.ptr;
@@ -357,28 +408,31 @@ TkWorkspace ws_view(const tk_tree* t, bool leaf) {
   return w;
 }
 
-// Grid of a launch with njobs jobs: persistent (at most the resident CTAs),
-// and no more CTAs than needed (a stitch CTA runs one job per warp at a time).
-int grid_for(tk_tree* t, bool leaf, int njobs) {
+// Grid of a stitch launch with njobs jobs: persistent (at most the resident
+// CTAs), and no more CTAs than jobs (a stitch CTA runs one job at a time).
+int grid_for(tk_tree* t, int njobs) {
   const int dtype = t->cfg.dtype;
   const int warps = stitch_warps(t);
-  const size_t smem = leaf ? tk_leaf_smem_bytes(dtype, t->nsm_leaf)
-                           : tk_stitch_smem_bytes(dtype, (size_t)t->nsm_stitch);
-  int occ = tk_occupancy(dtype, leaf ? 0 : 1, smem, leaf ? TK_NT : 32 * warps);
+  const size_t smem = tk_stitch_smem_bytes(dtype, (size_t)t->nsm_stitch);
+  int occ = tk_occupancy(dtype, smem, 32 * warps);
   if (occ < 1) occ = 1;
-  const int need = njobs;
-  return std::max(1, std::min(need, occ * t->sm_count));
+  return std::max(1, std::min(njobs, occ * t->sm_count));
 }
 
 // Decompose leaf blocks [first, first+njobs) read from raw (block stride in
-// elements), each of `ell` slices.
+// elements), each of `ell` slices: one cluster per block, persistent.
 int run_leaves(tk_tree* t, const void* raw, int64_t block_stride, int64_t first, int njobs, int ell) {
   if (njobs <= 0) return TK_OK;
   if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
-  const int grid = grid_for(t, true, njobs);
-  int rc = ensure_ws_leaf(t, grid);
+  int64_t per = 0;
+  const TkLeafLayout probe = leaf_layout(t, t->nsm_leaf, &per);
+  int maxc = tk_leaf_max_clusters(t->cfg.dtype, tk_leaf_smem_bytes(t->cfg.dtype, probe.nsm, probe.neig));
+  if (maxc < 1) maxc = 1;
+  const int ncl = std::min(njobs, maxc);
+  TkLeafLayout ly{};
+  int rc = ensure_ws_leaf(t, ncl, &ly);
   if (rc) return rc;
-  rc = tk_launch_leaf(t->cfg.dtype, make_view(t), raw, block_stride, first, njobs, ell, ws_view(t, true), grid,
+  rc = tk_launch_leaf(t->cfg.dtype, make_view(t), raw, block_stride, first, njobs, ell, ws_view(t, true), ly, ncl,
                       t->stream);
   t->launches += 1;
   return rc;
@@ -387,7 +441,7 @@ int run_leaves(tk_tree* t, const void* raw, int64_t block_stride, int64_t first,
 int run_merges(tk_tree* t, int level, int64_t k0, int njobs) {
   if (njobs <= 0) return TK_OK;
   if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
-  const int grid = grid_for(t, false, njobs);
+  const int grid = grid_for(t, njobs);
   int rc = ensure_ws_stitch(t, grid);
   if (rc) return rc;
   rc = tk_launch_merge(t->cfg.dtype, make_view(t), level, k0, njobs, ws_view(t, false), grid, t->stream);
@@ -426,10 +480,10 @@ int64_t out_elems(const tk_tree* t, int64_t L, const int* rq) {
 // One batch launch sequence (plan, heavy part on the side stream, light part)
 // with all pointers on the device.  Asynchronous on the tree's stream.
 int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_offsets, const int* rq, void* d_out,
-                 tk_query_info* d_info) {
+                 tk_query_info* d_info, const int64_t* d_tq = nullptr) {
   int rc = TK_OK;
   if (t->nsm_stitch == 0) t->nsm_stitch = pick_nsm_stitch(t);
-  const int grid = grid_for(t, false, n);
+  const int grid = grid_for(t, n);
   rc = ensure_ws_stitch(t, grid);
   if (rc) return rc;
   TkQueryBatch qb{};
@@ -439,6 +493,7 @@ int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_of
   qb.out = d_out;
   qb.info = d_info;
   qb.order = nullptr;
+  qb.tq = d_tq;
   for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
   if (n > 1) {
     // longest-first order; the heavy head of it runs on the side stream in
@@ -458,7 +513,7 @@ int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_of
     if (rc) return rc;
     int* split = (int*)t->plan.ptr;
     int* order = split + 4;
-    rc = tk_launch_plan(make_view(t), n, d_ranges, heavy_hits(t), split, order, t->stream);
+    rc = tk_launch_plan(make_view(t), n, d_ranges, d_tq, heavy_hits(t), split, order, t->stream);
     t->launches += 1;
     if (rc) return rc;
     qb.order = order;
@@ -801,9 +856,13 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
 }  // extern "C"
 
 // Batched queries with every pointer on the device, reports included;
-// asynchronous.  Used by the serving runtime (tk_server.cu).
+// asynchronous.  Used by the serving runtime (tk_server.cu).  d_tq (device, n,
+// may be null) gives the T each query is answered at; the open block is
+// decomposed first only when need_tail is set (some query reaches into the
+// current open block).
 int tk_query_batch_device(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_offsets,
-                          const int32_t* ranks, void* d_out, tk_query_info* d_info) {
+                          const int32_t* ranks, void* d_out, tk_query_info* d_info, const int64_t* d_tq,
+                          bool need_tail) {
   if (!t || n < 0) return TK_ERR_ARG;
   if (n == 0) return TK_OK;
   DeviceGuard g(t->dev);
@@ -811,9 +870,11 @@ int tk_query_batch_device(tk_tree* t, int n, const int64_t* d_ranges, const int6
   int rc = check_ranks(t, ranks, rq);
   if (rc) return rc;
   if (t->T == 0) return TK_ERR_RANGE;
-  rc = ensure_tail(t);
-  if (rc) return rc;
-  return launch_batch(t, n, d_ranges, d_offsets, rq, d_out, d_info);
+  if (need_tail) {
+    rc = ensure_tail(t);
+    if (rc) return rc;
+  }
+  return launch_batch(t, n, d_ranges, d_offsets, rq, d_out, d_info, d_tq);
 }
 
 cudaStream_t tk_tree_stream(const tk_tree* t) { return t->stream; }
@@ -942,7 +1003,7 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
   if (t->T == 0) return TK_ERR_RANGE;
   const int warps = stitch_warps(t);
   const int fit = (int)std::min<size_t>((TK_NOALLOC_SCRATCH_BYTES - head) / per_cta_bytes, 1 << 20);
-  const int grid = std::max(1, std::min(grid_for(t, false, n), fit));
+  const int grid = std::max(1, std::min(grid_for(t, n), fit));
   char* base = (char*)d.ptr;
   rc = cuda_ok(cudaMemsetAsync(base, 0, 256, t->stream));  // status word starts at zero
   if (rc) return rc;

@@ -8,7 +8,7 @@
 #define TK_MAXP TK_MAX_MODES
 #define TK_MAXL 40      // tree levels (2^39 leaf blocks)
 #define TK_MAXH 64      // hits per stitch job handled by the kernel
-#define TK_NT 256       // threads per CTA of the leaf kernel; stitch CTAs are <= TK_NT
+#define TK_NT 256       // threads per CTA of the leaf kernel
 #define TK_HITREC_BYTES 160  // bytes of one hit record in a stitch job's workspace
 
 // Device view of a tree: dimensions, the implicit dyadic node numbering and
@@ -43,9 +43,9 @@ struct TkTreeView {
 
 struct TkWorkspace {
   void* base;              // per-worker chunks of `per_cta` elements (a worker is a
-                           // warp in k_stitch and a CTA in k_leaf)
-  int64_t per_cta;
-  int nsm;                 // k_leaf: largest eig order kept in shared memory
+                           // CTA in k_stitch and a cluster in k_leaf)
+  int64_t per_cta;         // elements per worker (k_leaf: per cluster)
+  int nsm;                 // unused by the current kernels
   int warps;               // warps per CTA of k_stitch
   size_t smem_arena;       // k_stitch: bytes of the per-job shared arena
   int* status;             // first device-side error (0 = none)
@@ -64,25 +64,53 @@ struct TkQueryBatch {
   const int* split;        // device: number of leading entries of `order` in part 1
   int part;                // 0: jobs [0, n); 1: jobs [0, *split); 2: jobs [*split, n)
   int rq[TK_MAXP];         // requested ranks
+  const int64_t* tq;       // device, n (may be null): the T each query is answered at
+                           // (<= the tree's T; a query must not reach into that T's open block
+                           // unless it is the tree's current T)
 };
 
-// Launchers (tk_kernels.cu).  All asynchronous on `stream`.
+#define TK_LEAF_CL 8  // CTAs of the thread-block cluster that decomposes one leaf block
+
+// Workspace of one leaf cluster: element offsets into its chunk, computed on
+// the host from the build dimensions and ranks (upper bounds for any block).
+struct TkLeafLayout {
+  int64_t U[TK_MAXP];      // factor of mode n: D_n x r_n (mode 0: B x r_1)
+  int64_t Vs[TK_MAXP];     // saved eigenbasis of mode n (D_n x D_n), the warm start
+  int64_t part[TK_MAXP];   // TK_LEAF_CL partial Grams of mode n (D_n x D_n each)
+  int64_t norm;            // TK_LEAF_CL partial squared norms
+  int64_t flag;            // stop flag of the ALS loop
+  int64_t Y;               // mat_n(Y_n), D_n x prod_{m!=n} r_m, row-major
+  int64_t G;               // core
+  int64_t cta, cta_stride; // per-CTA regions: start and size
+  // offsets within a CTA region
+  int64_t slab, b0, b1;    // gathered slab of X and the TTM chain buffers
+  int64_t T;               // warm-start product of the eigensolver
+  int64_t A, V, w, cs, pq; // eigensolver arrays when they do not fit shared memory
+  int64_t half;            // entries of each rotation array (order / 2 + 2)
+  int nsm;                 // largest eig order kept in shared memory
+  int neig;                // largest Gram order of a block
+  int eig_in_smem;
+};
+
+// Launchers (tk_kernels.cu, tk_leaf.cu).  All asynchronous on `stream`.
+// k_leaf runs nclusters clusters of TK_LEAF_CL CTAs over njobs blocks.
 int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t block_stride,
-                   int64_t first_block, int njobs, int ell, const TkWorkspace& ws, int grid,
-                   cudaStream_t stream);
+                   int64_t first_block, int njobs, int ell, const TkWorkspace& ws,
+                   const TkLeafLayout& ly, int nclusters, cudaStream_t stream);
+size_t tk_leaf_smem_bytes(int dtype, int nsm, int neig);
+int tk_leaf_max_clusters(int dtype, size_t smem);
 int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int njobs,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
 int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
 // order[0..n) longest first; *split = how many queries have >= heavy_hits hits.
-int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int heavy_hits, int* split, int* order,
-                   cudaStream_t stream);
+int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, const int64_t* tq, int heavy_hits, int* split,
+                   int* order, cudaStream_t stream);
 int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit* out, int cap,
                      int* counts, cudaStream_t stream);
 
-// Shared-memory bytes of the two kernel families for a given in-smem eig order.
+// Shared-memory bytes of a stitch CTA with a job arena of `arena` bytes.
 size_t tk_stitch_smem_bytes(int dtype, size_t arena);
-size_t tk_leaf_smem_bytes(int dtype, int nsm);
-int tk_occupancy(int dtype, int which /*0 leaf, 1 stitch*/, size_t smem, int threads);
+int tk_occupancy(int dtype, size_t smem, int threads);  // stitch CTAs per SM
 
 enum { TK_DEV_ERR_WORKSPACE = 1, TK_DEV_ERR_HITS = 2, TK_DEV_ERR_RANGE = 3 };

@@ -5,7 +5,7 @@
 //            range query (Section 6.1: Recall, Eq. (partial-tucker),
 //            Algorithm 2) or the re-decomposition of a newly complete node
 //            from its two children (Algorithm 3, Stitch).
-//  k_leaf    one CTA per leaf block: Tucker-ALS (Section 2) of the raw block.
+//  (k_leaf, the leaf blocks' Tucker-ALS, is in tk_leaf.cu.)
 //
 // Stitch runs in coefficient space.  Every V~_i^(1) has orthonormal columns
 // and the hits occupy disjoint time rows, so Z^(1) of Eq. (stitch-temp-2)
@@ -74,7 +74,6 @@ template <class S> struct WarpSm {
   S thr;
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Shared bytes of one job group: the header, then `arena` bytes into which
 // the job places its hottest buffers (the rest goes to its global chunk).
@@ -82,71 +81,50 @@ template <class S> __host__ __device__ inline size_t group_smem_bytes(size_t are
   return align16(sizeof(WarpSm<S>)) + align16(arena);
 }
 
-constexpr int kLeafHdr = 640;  // bytes reserved for the leaf kernel's shared header
 
 __device__ __forceinline__ int64_t node_lo_of(const TkTreeView& tv, int j, int64_t k) {
   return (k << j) * (int64_t)tv.B;
 }
 
-// Algorithm 1 (Recall) on the implicit tree; writes up to cap hits in time
-// order.  theta test in integers: theta_den * overlap >= theta_num * |v|.
-// Leaves are terminal: an overlapping leaf (complete or tail) is a hit.
-// Returns the hit count, or -1 if more than cap hits were found.
-__device__ int recall_dev(const TkTreeView& tv, int64_t ts, int64_t te, HitRec* hits, int cap) {
-  if (tv.height <= 0) return 0;
-  int sj[2 * TK_MAXL + 4];
-  int64_t sk[2 * TK_MAXL + 4];
-  int sp = 0, nh = 0;
-  sj[0] = tv.height - 1;
-  sk[0] = 0;
-  sp = 1;
-  while (sp > 0) {
-    --sp;
-    const int j = sj[sp];
-    const int64_t k = sk[sp];
-    const int64_t w = ((int64_t)1 << j) * tv.B;
-    const int64_t lo = k * w;
-    int64_t hi = lo + w;
-    if (hi > tv.T) hi = tv.T;
-    const int64_t a = ts > lo ? ts : lo, b = te < hi ? te : hi;
-    const int64_t ov = b > a ? b - a : 0;
-    const bool complete = ((k + 1) << j) <= tv.nb;
-    bool hit = false;
-    if (j == 0) hit = (k < tv.nbt) && ov > 0;
-    else if (complete) hit = (int64_t)tv.theta_den * ov >= (int64_t)tv.theta_num * (hi - lo);
-    if (hit) {
-      if (nh >= cap) return -1;
-      HitRec& h = hits[nh++];
-      h.level = j;
-      h.index = k;
-      h.node_lo = lo;
-      h.node_hi = hi;
-      h.lo = a;
-      h.hi = b;
-      h.partial = (a != lo || b != hi) ? 1 : 0;
-      continue;
-    }
-    if (j == 0) continue;
-    const int64_t mu = (2 * k + 1) * (w / 2);
-    if (te <= mu) {
-      sj[sp] = j - 1; sk[sp] = 2 * k; ++sp;
-    } else if (ts >= mu) {
-      sj[sp] = j - 1; sk[sp] = 2 * k + 1; ++sp;
-    } else {
-      sj[sp] = j - 1; sk[sp] = 2 * k + 1; ++sp;
-      sj[sp] = j - 1; sk[sp] = 2 * k; ++sp;
-    }
-  }
-  return nh;
+// The tree as of T slices: complete blocks, blocks including the tail, and
+// the height of Section 4.2.  Nodes complete at T stay unchanged by later
+// appends, so a query can be answered against an earlier T as long as it
+// does not reach into that T's open block.
+struct TkEpoch {
+  int64_t T, nb, nbt;
+  int height;
+};
+
+__device__ __forceinline__ TkEpoch epoch_at(const TkTreeView& tv, int64_t T) {
+  TkEpoch e;
+  e.T = T;
+  e.nb = T / tv.B;
+  e.nbt = (T + tv.B - 1) / tv.B;
+  e.height = e.nbt > 0 ? (e.nbt > 1 ? 64 - __clzll((unsigned long long)(e.nbt - 1)) : 0) + 1 : 0;
+  return e;
 }
 
-// Size of Algorithm 1's hit set (same traversal as recall_dev, no records).
-__device__ int recall_count(const TkTreeView& tv, int64_t ts, int64_t te) {
-  if (tv.height <= 0 || !(ts >= 0 && ts < te && te <= tv.T)) return 0;
+__device__ __forceinline__ TkEpoch epoch_now(const TkTreeView& tv) {
+  TkEpoch e;
+  e.T = tv.T;
+  e.nb = tv.nb;
+  e.nbt = tv.nbt;
+  e.height = tv.height;
+  return e;
+}
+
+// Algorithm 1 (Recall) on the implicit tree as of epoch ep; with REC, writes
+// up to cap hits in time order.  theta test in integers: theta_den * overlap
+// >= theta_num * |v|.  Leaves are terminal: an overlapping leaf (complete or
+// tail) is a hit.  Returns the hit count, or -1 if more than cap hits were
+// found (REC only).
+template <bool REC>
+__device__ int recall_walk(const TkTreeView& tv, const TkEpoch& ep, int64_t ts, int64_t te, HitRec* hits, int cap) {
+  if (ep.height <= 0) return 0;
   int sj[2 * TK_MAXL + 4];
   int64_t sk[2 * TK_MAXL + 4];
   int sp = 1, nh = 0;
-  sj[0] = tv.height - 1;
+  sj[0] = ep.height - 1;
   sk[0] = 0;
   while (sp > 0) {
     --sp;
@@ -155,14 +133,25 @@ __device__ int recall_count(const TkTreeView& tv, int64_t ts, int64_t te) {
     const int64_t w = ((int64_t)1 << j) * tv.B;
     const int64_t lo = k * w;
     int64_t hi = lo + w;
-    if (hi > tv.T) hi = tv.T;
+    if (hi > ep.T) hi = ep.T;
     const int64_t a = ts > lo ? ts : lo, b = te < hi ? te : hi;
     const int64_t ov = b > a ? b - a : 0;
-    const bool complete = ((k + 1) << j) <= tv.nb;
+    const bool complete = ((k + 1) << j) <= ep.nb;
     bool hit = false;
-    if (j == 0) hit = (k < tv.nbt) && ov > 0;
+    if (j == 0) hit = (k < ep.nbt) && ov > 0;
     else if (complete) hit = (int64_t)tv.theta_den * ov >= (int64_t)tv.theta_num * (hi - lo);
     if (hit) {
+      if (REC) {
+        if (nh >= cap) return -1;
+        HitRec& h = hits[nh];
+        h.level = j;
+        h.index = k;
+        h.node_lo = lo;
+        h.node_hi = hi;
+        h.lo = a;
+        h.hi = b;
+        h.partial = (a != lo || b != hi) ? 1 : 0;
+      }
       ++nh;
       continue;
     }
@@ -178,6 +167,16 @@ __device__ int recall_count(const TkTreeView& tv, int64_t ts, int64_t te) {
     }
   }
   return nh;
+}
+
+__device__ int recall_dev(const TkTreeView& tv, const TkEpoch& ep, int64_t ts, int64_t te, HitRec* hits, int cap) {
+  return recall_walk<true>(tv, ep, ts, te, hits, cap);
+}
+
+// Size of Algorithm 1's hit set; 0 for an invalid range.
+__device__ int recall_count(const TkTreeView& tv, const TkEpoch& ep, int64_t ts, int64_t te) {
+  if (!(ts >= 0 && ts < te && te <= ep.T)) return 0;
+  return recall_walk<false>(tv, ep, ts, te, nullptr, 0);
 }
 
 __device__ void set_err(int* status, int code) { atomicCAS(status, 0, code); }
@@ -223,7 +222,8 @@ __device__ void proj_coef(const S* E, int cm, int rom, const S* R, int km, int k
 // group's workspace chunk (ws_cap elements); the hit records occupy its
 // first TK_MAXH entries.
 template <class G, class S>
-__device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t te, int mlevel, int64_t mindex,
+__device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, int64_t ts, int64_t te, int mlevel,
+                           int64_t mindex,
                            const int* rq, S* ws, int64_t ws_cap, size_t arena_bytes, S* core_dst, S* u0_dst,
                            int64_t ld0,
                            S* const* un_dst, const int64_t* ldn, int* ranks_dst, tk_query_info* info,
@@ -242,7 +242,7 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
     cx.err = 0;
     int nh = 0;
     if (mode == TK_JOB_QUERY) {
-      nh = recall_dev(tv, ts, te, hits, TK_MAXH);
+      nh = recall_dev(tv, ep, ts, te, hits, TK_MAXH);
       if (nh < 0) cx.err = TK_DEV_ERR_HITS;
     } else {
       nh = 2;
@@ -402,8 +402,10 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
   bool have_v[TK_MAXP];
   for (int n = 0; n < TK_MAXP; ++n) have_v[n] = false;
   int sweeps = 0;
+  long long eig_cyc = 0, qr_cyc = 0;
   // eigenvectors of the order-nsz matrix in A, warm-started from the mode's previous basis
   auto eig = [&](int mode_n, int nsz) {
+    const long long c0 = clock64();
     const int rkeep = cx.ro[mode_n];
     S* Vs = cx.Vs[mode_n];
     const bool warm = have_v[mode_n];
@@ -415,6 +417,7 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
     for (int i = lane; i < nsz * nsz; i += nt) Vs[i] = V[i];
     G::sync();
     have_v[mode_n] = true;
+    eig_cyc += clock64() - c0;
   };
   int dims[TK_MAXP];
 
@@ -452,7 +455,9 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
         sl[idx] = tf[(h.lo + t) * tv.r[0] + c];
       }
       G::sync();
+      const long long c0 = clock64();
       householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc);
+      qr_cyc += clock64() - c0;
       int tot = 1;
       for (int n = 0; n < p; ++n) {
         dims[n] = nr[n];
@@ -497,7 +502,9 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
       }
     }
     G::sync();
+    const long long c0 = clock64();
     householder_qr<G, S>(Phi, Dn, kn, kn, cx.tau[n], sm.sc);
+    qr_cyc += clock64() - c0;
     S* R = cx.R[n];
     for (int idx = lane; idx < cn * kn; idx += nt) {
       const int a = idx / kn, b = idx % kn;
@@ -661,6 +668,8 @@ __device__ void stitch_job(const TkTreeView& tv, int mode, int64_t ts, int64_t t
       info->eig_sweeps = sweeps;
       info->eig_max_order = cx.neig;
       info->device_cycles = (int64_t)(clock64() - t_start);
+      info->eig_cycles = (int64_t)eig_cyc;
+      info->qr_cycles = (int64_t)qr_cyc;
     }
   }
   G::sync();
@@ -695,7 +704,8 @@ __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, i
       const int64_t ts = qb.ranges[2 * q], te = qb.ranges[2 * q + 1];
       S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[q];
       tk_query_info* info = qb.info ? qb.info + q : nullptr;
-      if (!(ts >= 0 && ts < te && te <= tv.T)) {
+      const TkEpoch ep = (qb.tq && qb.tq[q] <= tv.T) ? epoch_at(tv, qb.tq[q]) : epoch_now(tv);
+      if (!(ts >= 0 && ts < te && te <= ep.T)) {
         if (tid == 0) {
           set_err(wsd.status, TK_DEV_ERR_RANGE);
           if (info) info->iters = -TK_DEV_ERR_RANGE;
@@ -714,7 +724,7 @@ __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, i
         ldn[n] = qb.rq[n];
         cur += (int64_t)tv.D[n] * qb.rq[n];
       }
-      stitch_job<G, S>(tv, mode, ts, te, 0, 0, qb.rq, ws, wsd.per_cta, wsd.smem_arena, out, u0, qb.rq[0], un,
+      stitch_job<G, S>(tv, ep, mode, ts, te, 0, 0, qb.rq, ws, wsd.per_cta, wsd.smem_arena, out, u0, qb.rq[0], un,
                        ldn, nullptr, info, wsd.status, gsm);
     } else {
       const int64_t k = k0 + job;
@@ -727,213 +737,10 @@ __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, i
         un[n] = reinterpret_cast<S*>(tv.fac_pool[n]) + slot * tv.fac_stride[n];
         ldn[n] = tv.r[n];
       }
-      stitch_job<G, S>(tv, mode, 0, 0, level, k, tv.r, ws, wsd.per_cta, wsd.smem_arena, core, u0, tv.r[0], un,
+      stitch_job<G, S>(tv, epoch_now(tv), mode, 0, 0, level, k, tv.r, ws, wsd.per_cta, wsd.smem_arena, core, u0,
+                       tv.r[0], un,
                        ldn, tv.node_ranks + slot * TK_MAXP, nullptr, wsd.status, gsm);
     }
-  }
-}
-
-// ---- leaf blocks: Tucker-ALS of Section 2 on the raw block, one CTA each ----
-template <class S>
-__global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int64_t block_stride,
-                                                int64_t first_block, int njobs, int ell, TkWorkspace wsd) {
-  using BG = BlockGroup;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  struct LeafSm {
-    S red[40];
-    S sc[4];
-    int flag;
-    int nsw;
-    S thr;
-    int rl[TK_MAXP];
-    int64_t off_U[TK_MAXP], off_Vs[TK_MAXP], off_b0, off_b1, off_G, off_T, off_A, off_V, off_w, off_cs, off_pq;
-    int err, eig_in_smem;
-  };
-  static_assert(sizeof(LeafSm) <= kLeafHdr, "leaf shared header");
-  LeafSm& sm = *reinterpret_cast<LeafSm*>(smem_raw);
-  const int nsm = wsd.nsm;
-  const int half_cap = nsm / 2 + 2;
-  int* js_pq = reinterpret_cast<int*>(smem_raw + kLeafHdr);
-  S* js_c = reinterpret_cast<S*>(smem_raw + kLeafHdr + align16(half_cap * sizeof(int)));
-  S* js_s = js_c + half_cap;
-  S* js_w = js_s + half_cap;
-  S* sA = js_w + nsm + 2;
-  S* sV = sA + nsm * nsm;
-  S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
-  const int p = tv.p;
-  const int tid = threadIdx.x;
-  const int maxsw = sizeof(S) == 8 ? 24 : 16;
-  for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
-    const int64_t b = first_block + job;
-    const S* X = raw + (int64_t)job * block_stride;
-    const int64_t slot = tv.level_base[0] + b;
-    int xd[TK_MAXP];
-    xd[0] = ell;
-    for (int n = 1; n < p; ++n) xd[n] = tv.D[n];
-    if (tid == 0) {
-      // rank clamp: min(r_n, extent_n), then r_n <= prod_{m!=n} r_m
-      for (int n = 0; n < p; ++n) sm.rl[n] = tv.r[n] < xd[n] ? tv.r[n] : xd[n];
-      bool ch = true;
-      while (ch) {
-        ch = false;
-        for (int n = 0; n < p; ++n) {
-          int64_t pr = 1;
-          for (int m = 0; m < p; ++m)
-            if (m != n) pr *= sm.rl[m];
-          if (sm.rl[n] > pr) {
-            sm.rl[n] = (int)pr;
-            ch = true;
-          }
-        }
-      }
-      int64_t cur = 0;
-      auto take = [&](int64_t nel) {
-        const int64_t o = cur;
-        cur += (nel + 31) & ~(int64_t)31;
-        return o;
-      };
-      int neig = 0;
-      for (int n = 0; n < p; ++n) {
-        sm.off_U[n] = take((int64_t)xd[n] * sm.rl[n]);
-        sm.off_Vs[n] = take((int64_t)xd[n] * xd[n]);
-        if (xd[n] > neig) neig = xd[n];
-      }
-      int64_t xel = 1;
-      for (int n = 0; n < p; ++n) xel *= xd[n];
-      sm.off_b0 = take(xel);
-      sm.off_b1 = take(xel);
-      int64_t gel = 1;
-      for (int n = 0; n < p; ++n) gel *= sm.rl[n];
-      sm.off_G = take(gel);
-      sm.off_T = take((int64_t)neig * neig);
-      sm.eig_in_smem = neig <= nsm;
-      if (!sm.eig_in_smem) {
-        sm.off_A = take((int64_t)neig * neig);
-        sm.off_V = take((int64_t)neig * neig);
-        sm.off_w = take(neig + 2);
-        sm.off_cs = take(2 * (neig / 2 + 2));
-        sm.off_pq = take(((neig / 2 + 2) * (int64_t)sizeof(int) + sizeof(S) - 1) / sizeof(S));
-      }
-      sm.err = cur > wsd.per_cta ? TK_DEV_ERR_WORKSPACE : 0;
-    }
-    __syncthreads();
-    if (sm.err) {
-      if (tid == 0) set_err(wsd.status, sm.err);
-      continue;
-    }
-    int rl[TK_MAXP];
-    for (int n = 0; n < p; ++n) rl[n] = sm.rl[n];
-    S* A = sm.eig_in_smem ? sA : ws + sm.off_A;
-    S* V = sm.eig_in_smem ? sV : ws + sm.off_V;
-    S* ew = sm.eig_in_smem ? js_w : ws + sm.off_w;
-    JacobiScratch<S> js;
-    if (sm.eig_in_smem) {
-      js.pq = js_pq;
-      js.c = js_c;
-      js.s = js_s;
-    } else {
-      int neig = 0;
-      for (int n = 0; n < p; ++n) neig = xd[n] > neig ? xd[n] : neig;
-      js.pq = reinterpret_cast<int*>(ws + sm.off_pq);
-      js.c = ws + sm.off_cs;
-      js.s = ws + sm.off_cs + (neig / 2 + 2);
-    }
-    js.flag = &sm.flag;
-    js.red = sm.red;
-    js.nsw = &sm.nsw;
-    js.thr = &sm.thr;
-    S* T = ws + sm.off_T;
-    bool have_v[TK_MAXP];
-    for (int n = 0; n < TK_MAXP; ++n) have_v[n] = false;
-    auto eig = [&](int mode_n, int nsz) {
-      S* Vs = ws + sm.off_Vs[mode_n];
-      const bool warm = have_v[mode_n];
-      if (warm) {
-        for (int i = tid; i < nsz * nsz; i += blockDim.x) V[i] = Vs[i];
-        __syncthreads();
-      }
-      jacobi_eig<BG, S>(nsz, rl[mode_n], A, V, T, warm, ew, js, maxsw);
-      for (int i = tid; i < nsz * nsz; i += blockDim.x) Vs[i] = V[i];
-      __syncthreads();
-      have_v[mode_n] = true;
-    };
-    S* b0 = ws + sm.off_b0;
-    S* b1 = ws + sm.off_b1;
-    int64_t xel = 1;
-    for (int n = 0; n < p; ++n) xel *= xd[n];
-    const S xn2 = sum_squares<BG, S>(X, xel, sm.red);
-    int dims[TK_MAXP];
-    // HOSVD start for modes 2..p
-    for (int n = 1; n < p; ++n) {
-      mode_gram<BG, S>(X, xd, p, n, A, xd[n], false);
-      eig(n, xd[n]);
-      select_top<BG, S>(xd[n], ew, V, rl[n], ws + sm.off_U[n], rl[n]);
-    }
-    S e_prev = S(-1), e = 0;
-    int it;
-    const int maxit = tv.max_iter > 0 ? tv.max_iter : 1;
-    for (it = 1; it <= maxit; ++it) {
-      for (int n = 0; n <= p; ++n) {  // n == p: the core
-        const S* src = X;
-        for (int m = 0; m < p; ++m) dims[m] = xd[m];
-        bool first = true;
-        for (int m = p - 1; m >= 0; --m) {
-          if (m == n) continue;
-          S* dst;
-          if (n == p && m == 0) dst = ws + sm.off_G;
-          else dst = first ? b0 : (src == b0 ? b1 : b0);
-          ttm<BG, S>(src, dims, p, m, ws + sm.off_U[m], 1, rl[m], rl[m], dst, false);
-          dims[m] = rl[m];
-          src = dst;
-          first = false;
-        }
-        if (n == p) break;
-        mode_gram<BG, S>(src, dims, p, n, A, xd[n], false);
-        eig(n, xd[n]);
-        select_top<BG, S>(xd[n], ew, V, rl[n], ws + sm.off_U[n], rl[n]);
-      }
-      int64_t gel = 1;
-      for (int m = 0; m < p; ++m) gel *= rl[m];
-      const S gn2 = sum_squares<BG, S>(ws + sm.off_G, gel, sm.red);
-      e = xn2 > S(0) ? sqrt(fmax(S(0), S(1) - gn2 / xn2)) : S(0);
-      if (tv.tol > 0 && it > 1 && fabs(e - e_prev) < (S)tv.tol) break;
-      e_prev = e;
-    }
-    // store: core (capacity dims r), temporal rows (ld r0), factors (ld r_n)
-    {
-      S* core = reinterpret_cast<S*>(tv.core_pool) + slot * tv.core_stride;
-      int ctot = 1;
-      for (int m = 0; m < p; ++m) ctot *= tv.r[m];
-      const S* Gc = ws + sm.off_G;
-      for (int idx = tid; idx < ctot; idx += blockDim.x) {
-        int rem = idx, src = 0, strd = 1;
-        bool inside = true;
-        for (int n = p - 1; n >= 0; --n) {
-          const int in = rem % tv.r[n];
-          rem /= tv.r[n];
-          if (in >= rl[n]) inside = false;
-          src += in * strd;
-          strd *= rl[n];
-        }
-        core[idx] = inside ? Gc[src] : S(0);
-      }
-      S* tf = reinterpret_cast<S*>(tv.tfac) + b * (int64_t)tv.B * tv.r[0];
-      const S* U0 = ws + sm.off_U[0];
-      for (int idx = tid; idx < ell * tv.r[0]; idx += blockDim.x) {
-        const int t = idx / tv.r[0], c = idx % tv.r[0];
-        tf[idx] = c < rl[0] ? U0[t * rl[0] + c] : S(0);
-      }
-      for (int n = 1; n < p; ++n) {
-        S* F = reinterpret_cast<S*>(tv.fac_pool[n]) + slot * tv.fac_stride[n];
-        const S* Un = ws + sm.off_U[n];
-        for (int idx = tid; idx < tv.D[n] * tv.r[n]; idx += blockDim.x) {
-          const int d = idx / tv.r[n], c = idx % tv.r[n];
-          F[idx] = c < rl[n] ? Un[d * rl[n] + c] : S(0);
-        }
-      }
-      if (tid < TK_MAXP) tv.node_ranks[slot * TK_MAXP + tid] = tid < p ? rl[tid] : 0;
-    }
-    __syncthreads();
   }
 }
 
@@ -941,14 +748,16 @@ __global__ void __launch_bounds__(TK_NT) k_leaf(TkTreeView tv, const S* raw, int
 // decreasing hit-set size (a proxy of their cost: the eigenproblem orders
 // grow with it), by a counting sort in one CTA.  Ties keep no particular order;
 // the order only schedules work (every query writes its own outputs).
-__global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, int heavy_hits, int* split, int* order) {
+__global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, const int64_t* tq, int heavy_hits, int* split,
+                       int* order) {
   constexpr int NB = TK_MAXH + 1;
   __shared__ int hist[NB];
   __shared__ int base[NB];
   for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    int c = recall_count(tv, ranges[2 * q], ranges[2 * q + 1]);
+    const TkEpoch ep = (tq && tq[q] <= tv.T) ? epoch_at(tv, tq[q]) : epoch_now(tv);
+    int c = recall_count(tv, ep, ranges[2 * q], ranges[2 * q + 1]);
     atomicAdd(&hist[c < NB ? c : NB - 1], 1);
   }
   __syncthreads();
@@ -963,7 +772,8 @@ __global__ void k_plan(TkTreeView tv, int n, const int64_t* ranges, int heavy_hi
   }
   __syncthreads();
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    int c = recall_count(tv, ranges[2 * q], ranges[2 * q + 1]);
+    const TkEpoch ep = (tq && tq[q] <= tv.T) ? epoch_at(tv, tq[q]) : epoch_now(tv);
+    int c = recall_count(tv, ep, ranges[2 * q], ranges[2 * q + 1]);
     const int pos = atomicAdd(&base[c < NB ? c : NB - 1], 1);
     order[pos] = q;
   }
@@ -973,7 +783,7 @@ __global__ void k_hitset(TkTreeView tv, int n, const int64_t* ranges, tk_hit* ou
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   HitRec hits[TK_MAXH];
-  const int nh = recall_dev(tv, ranges[2 * q], ranges[2 * q + 1], hits, TK_MAXH);
+  const int nh = recall_dev(tv, epoch_now(tv), ranges[2 * q], ranges[2 * q + 1], hits, TK_MAXH);
   counts[q] = nh;
   for (int i = 0; i < nh && i < cap; ++i) {
     tk_hit& o = out[(int64_t)q * cap + i];
@@ -991,21 +801,12 @@ __global__ void k_hitset(TkTreeView tv, int n, const int64_t* ranges, tk_hit* ou
 
 using namespace tk;
 
-static size_t leaf_smem(size_t es, int nsm) {
-  const int half_cap = nsm / 2 + 2;
-  size_t b = kLeafHdr + align16(half_cap * sizeof(int));
-  b += es * (2 * half_cap + nsm + 2 + 2 * (size_t)nsm * nsm);
-  return b + 64;
-}
-
 // Dynamic shared bytes of a k_stitch CTA (one job group per CTA).
 size_t tk_stitch_smem_bytes(int dtype, size_t arena) {
   return dtype == TK_F64 ? group_smem_bytes<double>(arena) : group_smem_bytes<float>(arena);
 }
-size_t tk_leaf_smem_bytes(int dtype, int nsm) { return leaf_smem(dtype == TK_F64 ? 8 : 4, nsm); }
 
 template <class S> static const void* stitch_fn() { return (const void*)k_stitch<S, BlockGroup>; }
-template <class S> static const void* leaf_fn() { return (const void*)k_leaf<S>; }
 
 static int set_smem_attr(const void* fn, size_t smem) {
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -1013,27 +814,12 @@ static int set_smem_attr(const void* fn, size_t smem) {
   return TK_OK;
 }
 
-int tk_occupancy(int dtype, int which, size_t smem, int threads) {
-  const void* fn = which == 0 ? (dtype == TK_F64 ? leaf_fn<double>() : leaf_fn<float>())
-                              : (dtype == TK_F64 ? stitch_fn<double>() : stitch_fn<float>());
+int tk_occupancy(int dtype, size_t smem, int threads) {
+  const void* fn = dtype == TK_F64 ? stitch_fn<double>() : stitch_fn<float>();
   if (set_smem_attr(fn, smem) != TK_OK) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) return 0;
   return nb;
-}
-
-int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t block_stride, int64_t first_block,
-                   int njobs, int ell, const TkWorkspace& ws, int grid, cudaStream_t stream) {
-  if (njobs <= 0) return TK_OK;
-  const size_t smem = tk_leaf_smem_bytes(dtype, ws.nsm);
-  if (dtype == TK_F64) {
-    if (set_smem_attr(leaf_fn<double>(), smem)) return TK_ERR_CUDA;
-    k_leaf<double><<<grid, TK_NT, smem, stream>>>(tv, (const double*)raw, block_stride, first_block, njobs, ell, ws);
-  } else {
-    if (set_smem_attr(leaf_fn<float>(), smem)) return TK_ERR_CUDA;
-    k_leaf<float><<<grid, TK_NT, smem, stream>>>(tv, (const float*)raw, block_stride, first_block, njobs, ell, ws);
-  }
-  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
 
 static int launch_stitch(int dtype, const TkTreeView& tv, int mode, int level, int64_t k0, int njobs,
@@ -1064,10 +850,10 @@ int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, con
   return launch_stitch(dtype, tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws, grid, stream);
 }
 
-int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, int heavy_hits, int* split, int* order,
-                   cudaStream_t stream) {
+int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, const int64_t* tq, int heavy_hits, int* split,
+                   int* order, cudaStream_t stream) {
   if (n <= 0) return TK_OK;
-  k_plan<<<1, 1024, 0, stream>>>(tv, n, ranges, heavy_hits, split, order);
+  k_plan<<<1, 1024, 0, stream>>>(tv, n, ranges, tq, heavy_hits, split, order);
   return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
 

@@ -1,14 +1,19 @@
 // Serving runtime: continuous batching of interleaved range queries and
 // stream appends over one tree (host side, one worker thread).
 //
-// Requests are executed in ticket (arrival) order, so a query sees every
-// append submitted before it (Section 3: a stream update extends the tensor
-// the following queries range over).  The worker admits the queries waiting
-// at the head of the queue into a batch, up to a query count and an output
-// memory budget, and launches it as one batched stitch launch.  Two batch
-// slots alternate: the next batch is enqueued on the stream while the current
-// one runs, so requests that arrive during a launch are admitted to the next
-// one and the GPU is fed back to back.  Appends are applied between batches.
+// Requests take effect in ticket (arrival) order: a query sees every append
+// submitted before it and none submitted after it (Section 3: a stream update
+// extends the tensor that later queries range over).  The worker scans the
+// queue in order.  An append is issued at once, in stream order, behind the
+// batches already running: it never waits for them.  A query joins the batch
+// being formed together with the T it was submitted at; the batch is answered
+// after the appends scanned before it, each query against its own T (nodes
+// that were complete at that T are still stored unchanged, see TkEpoch).  A
+// query that reaches into the open block of its T needs that block's current
+// decomposition, so the scan stops at the next append and the batch launches
+// first.  Batches are bounded by a query count and an output budget (the
+// device memory a batch may hold); two batch slots alternate, so the next
+// batch is enqueued while the current one runs.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -24,7 +29,8 @@
 #include "tk_internal.h"
 
 int tk_query_batch_device(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_offsets,
-                          const int32_t* ranks, void* d_out, tk_query_info* d_info);
+                          const int32_t* ranks, void* d_out, tk_query_info* d_info, const int64_t* d_tq,
+                          bool need_tail);
 cudaStream_t tk_tree_stream(const tk_tree* t);
 
 namespace {
@@ -46,9 +52,11 @@ struct Req {
   Clock::time_point submitted;
 };
 
+constexpr int kRing = 16;  // staging slots of appended slices
+
 struct Slot {
   void* d_out = nullptr;
-  int64_t* d_meta = nullptr;        // ranges (2n) then offsets (n+1)
+  int64_t* d_meta = nullptr;        // ranges (2n), offsets (n+1), then each query's T (n)
   tk_query_info* d_info = nullptr;
   void* h_out = nullptr;            // pinned
   int64_t* h_meta = nullptr;        // pinned
@@ -69,6 +77,12 @@ struct tk_server {
   int64_t slice_elems = 0;
   Slot slots[2];
   std::deque<int> busy_fifo;  // slot indices in launch order (worker thread only)
+  int64_t T_applied = 0;      // T after the appends issued so far (worker thread only)
+  // appended slices go host -> pinned ring -> device ring -> the tree's open block
+  void* h_ring = nullptr;
+  void* d_ring = nullptr;
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_next = 0;
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -134,23 +148,27 @@ void complete_slot(tk_server* s, Slot& sl) {
   s->cv_done.notify_all();
 }
 
-// Launch a batch of queries in a free slot (asynchronous).
-void launch(tk_server* s, Slot& sl, std::vector<Req*>& batch) {
+// Launch a batch of queries in a free slot (asynchronous).  tq[i] is the T
+// query i is answered at; need_tail: some query reaches into the open block.
+void launch(tk_server* s, Slot& sl, std::vector<Req*>& batch, const std::vector<int64_t>& tq, bool need_tail) {
   const int n = (int)batch.size();
   int64_t* rng = sl.h_meta;
   int64_t* offs = sl.h_meta + 2 * n;
+  int64_t* hq = sl.h_meta + 3 * n + 1;
   offs[0] = 0;
   for (int i = 0; i < n; ++i) {
     rng[2 * i] = batch[i]->ts;
     rng[2 * i + 1] = batch[i]->te;
     offs[i + 1] = offs[i] + batch[i]->elems;
+    hq[i] = tq[i];
   }
   // every query of a batch has the same requested ranks (see the batching rule)
   const int32_t* ranks = batch[0]->has_ranks ? batch[0]->ranks : nullptr;
-  int rc = cudaMemcpyAsync(sl.d_meta, sl.h_meta, sizeof(int64_t) * (3 * (size_t)n + 1), cudaMemcpyHostToDevice,
+  int rc = cudaMemcpyAsync(sl.d_meta, sl.h_meta, sizeof(int64_t) * (4 * (size_t)n + 1), cudaMemcpyHostToDevice,
                            s->stream) == cudaSuccess ? TK_OK : TK_ERR_CUDA;
   if (rc == TK_OK)
-    rc = tk_query_batch_device(s->t, n, sl.d_meta, sl.d_meta + 2 * n, ranks, sl.d_out, sl.d_info);
+    rc = tk_query_batch_device(s->t, n, sl.d_meta, sl.d_meta + 2 * n, ranks, sl.d_out, sl.d_info,
+                               sl.d_meta + 3 * n + 1, need_tail);
   if (rc == TK_OK)
     rc = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)offs[n] * s->es, cudaMemcpyDeviceToHost, s->stream) ==
                  cudaSuccess ? TK_OK : TK_ERR_CUDA;
@@ -171,6 +189,28 @@ void launch(tk_server* s, Slot& sl, std::vector<Req*>& batch) {
   s->batched_queries += n;
 }
 
+// Issue one append on the tree's stream, behind the work already enqueued.
+// Its ticket completes once the append is issued: every later query sees it.
+void issue_append(tk_server* s, Req* a) {
+  const size_t bytes = (size_t)s->slice_elems * s->es;
+  const int k = s->ring_next;
+  s->ring_next = (k + 1) % kRing;
+  char* h = (char*)s->h_ring + (size_t)k * bytes;
+  char* d = (char*)s->d_ring + (size_t)k * bytes;
+  // the host slot is free once its previous copy has run
+  int rc = cudaEventSynchronize(s->ring_ev[k]) == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+  if (rc == TK_OK) {
+    std::memcpy(h, a->slice.data(), bytes);
+    rc = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s->stream) == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+  }
+  if (rc == TK_OK) rc = cudaEventRecord(s->ring_ev[k], s->stream) == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+  if (rc == TK_OK) rc = tk_stream_append(s->t, d, TK_IO_DEVICE);
+  if (rc == TK_OK) s->T_applied += 1;
+  std::lock_guard<std::mutex> lk(s->mu);
+  finish_locked(s, a, rc, Clock::now());
+  s->cv_done.notify_all();
+}
+
 bool same_ranks(const Req* a, const Req* b) {
   if (a->has_ranks != b->has_ranks) return false;
   return !a->has_ranks || std::memcmp(a->ranks, b->ranks, sizeof(a->ranks)) == 0;
@@ -178,9 +218,11 @@ bool same_ranks(const Req* a, const Req* b) {
 
 void run(tk_server* s) {
   cudaSetDevice(s->tcfg.device);
+  const int64_t B = s->tcfg.leaf_slices;
   while (true) {
-    Req* app = nullptr;
-    std::vector<Req*> batch;
+    std::vector<Req*> apps, batch;
+    std::vector<int64_t> tq;
+    bool need_tail = false;
     int free_idx = -1;
     {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -192,45 +234,38 @@ void run(tk_server* s) {
       }
       if (!s->slots[0].busy) free_idx = 0;
       else if (!s->slots[1].busy) free_idx = 1;
-      if (!s->pending.empty() && free_idx >= 0) {
-        Req* front = s->pending.front();
-        if (front->kind == REQ_APPEND) {
-          if (!any_busy) {  // an append changes the tree: apply it between batches
-            app = front;
-            s->pending.pop_front();
-          }
-        } else {
-          int64_t elems = 0;
-          while (!s->pending.empty() && (int)batch.size() < s->cfg.max_batch) {
-            Req* r = s->pending.front();
-            if (r->kind != REQ_QUERY || !same_ranks(r, front)) break;
-            if (!batch.empty() && elems + r->elems > s->cfg.max_batch_out_elems) break;
-            elems += r->elems;
-            batch.push_back(r);
-            s->pending.pop_front();
-          }
+      // scan the queue in ticket order (see the header comment)
+      int64_t T = s->T_applied;
+      int64_t elems = 0;
+      while (!s->pending.empty()) {
+        Req* r = s->pending.front();
+        if (r->kind == REQ_APPEND) {
+          if (need_tail) break;
+          apps.push_back(r);
+          s->pending.pop_front();
+          ++T;
+          continue;
         }
+        if (free_idx < 0 || (int)batch.size() >= s->cfg.max_batch) break;
+        if (!batch.empty() && (!same_ranks(r, batch[0]) || elems + r->elems > s->cfg.max_batch_out_elems)) break;
+        elems += r->elems;
+        if (T % B != 0 && r->te > T / B * B) need_tail = true;
+        batch.push_back(r);
+        tq.push_back(T);
+        s->pending.pop_front();
       }
     }
-    if (app) {
-      int rc = tk_stream_append(s->t, app->slice.data(), TK_IO_HOST);
-      if (rc == TK_OK) rc = cudaStreamSynchronize(s->stream) == cudaSuccess ? TK_OK : TK_ERR_CUDA;
-      std::lock_guard<std::mutex> lk(s->mu);
-      finish_locked(s, app, rc, Clock::now());
-      s->cv_done.notify_all();
-      continue;
-    }
+    for (Req* a : apps) issue_append(s, a);
     if (!batch.empty()) {
-      launch(s, s->slots[free_idx], batch);
+      launch(s, s->slots[free_idx], batch, tq, need_tail);
       if (s->slots[free_idx].busy) s->busy_fifo.push_back(free_idx);
       continue;
     }
-    if (s->busy_fifo.empty()) continue;
+    if (!apps.empty() || s->busy_fifo.empty()) continue;
     Slot& oldest = s->slots[s->busy_fifo.front()];
     if (free_idx >= 0 && cudaEventQuery(oldest.done) == cudaErrorNotReady) {
-      // A slot is free and the oldest batch still runs.  With nothing queued,
-      // wait briefly for arrivals so that they can be enqueued behind it; an
-      // append at the head waits for the batches instead.
+      // A slot is free and the oldest batch still runs: with nothing queued,
+      // wait briefly for arrivals so that they can be enqueued behind it.
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->pending.empty() && !s->stop) {
         s->cv_work.wait_for(lk, std::chrono::microseconds(50));
@@ -240,6 +275,15 @@ void run(tk_server* s) {
     complete_slot(s, oldest);
     s->busy_fifo.pop_front();
   }
+}
+
+void free_ring(tk_server* s) {
+  if (s->h_ring) cudaFreeHost(s->h_ring);
+  if (s->d_ring) cudaFree(s->d_ring);
+  for (int k = 0; k < kRing; ++k)
+    if (s->ring_ev[k]) cudaEventDestroy(s->ring_ev[k]);
+  s->h_ring = s->d_ring = nullptr;
+  for (int k = 0; k < kRing; ++k) s->ring_ev[k] = nullptr;
 }
 
 void free_slot(Slot& sl) {
@@ -275,6 +319,7 @@ int tk_server_create(tk_tree* t, const tk_server_config* cfg, tk_server** out) {
   s->stream = tk_tree_stream(t);
   s->es = s->tcfg.dtype == TK_F64 ? 8 : 4;
   s->T_submitted = tk_timespan(t);
+  s->T_applied = s->T_submitted;
   s->slice_elems = 1;
   for (int n = 1; n < s->tcfg.p; ++n) s->slice_elems *= s->tcfg.dims[n];
   cudaSetDevice(s->tcfg.device);
@@ -282,16 +327,22 @@ int tk_server_create(tk_tree* t, const tk_server_config* cfg, tk_server** out) {
   for (Slot& sl : s->slots) {
     const size_t nb = (size_t)c.max_batch;
     ok = ok && cudaMalloc(&sl.d_out, (size_t)c.max_batch_out_elems * s->es) == cudaSuccess;
-    ok = ok && cudaMalloc((void**)&sl.d_meta, sizeof(int64_t) * (3 * nb + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&sl.d_meta, sizeof(int64_t) * (4 * nb + 1)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&sl.d_info, sizeof(tk_query_info) * nb) == cudaSuccess;
     ok = ok && cudaMallocHost(&sl.h_out, (size_t)c.max_batch_out_elems * s->es) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&sl.h_meta, sizeof(int64_t) * (3 * nb + 1)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&sl.h_meta, sizeof(int64_t) * (4 * nb + 1)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&sl.h_info, sizeof(tk_query_info) * nb) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
   }
+  const size_t ring_bytes = (size_t)kRing * s->slice_elems * s->es;
+  ok = ok && cudaMallocHost(&s->h_ring, ring_bytes) == cudaSuccess;
+  ok = ok && cudaMalloc(&s->d_ring, ring_bytes) == cudaSuccess;
+  for (int k = 0; k < kRing; ++k)
+    ok = ok && cudaEventCreateWithFlags(&s->ring_ev[k], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     for (Slot& sl : s->slots) free_slot(sl);
+    free_ring(s);
     delete s;
     return TK_ERR_NOMEM;
   }
@@ -416,6 +467,7 @@ void tk_server_destroy(tk_server* s) {
   cudaSetDevice(s->tcfg.device);
   cudaStreamSynchronize(s->stream);
   for (Slot& sl : s->slots) free_slot(sl);
+  free_ring(s);
   for (Req* r : s->pending) delete r;
   delete s;
 }
