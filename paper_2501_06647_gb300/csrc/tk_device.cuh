@@ -514,6 +514,272 @@ __device__ int jacobi_eig(int n, int r, S* A, S* V, S* T, bool warm, S* w, Jacob
   return jacobi_sweeps<G, S>(n, r, A, V, floor_abs, w, js, max_sweeps);
 }
 
+template <class S> struct Tiny;
+template <> struct Tiny<float> { static __device__ __forceinline__ float v() { return 1.1754944e-38f; } };
+template <> struct Tiny<double> { static __device__ __forceinline__ double v() { return 2.2250738585072014e-308; } };
+
+// Division in the Sturm recurrence: the count only needs the sign pattern,
+// so FP32 uses the fast approximate quotient; FP64 divides exactly.
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+
+// Orders from which trd_eig replaces the Jacobi method, and its largest r.
+constexpr int kTrdMinOrder = 20;
+constexpr int kTrdMaxRank = 62;
+
+// Elements of the vector scratch of trd_eig for order n, r vectors and nw
+// warps in the group.
+__host__ __device__ inline int trd_scratch_elems(int n, int r, int nw) {
+  const int wv = nw < r ? nw : r;
+  return 6 * n + 2 * r + 8 + 6 * n * (wv > 0 ? wv : 1);
+}
+
+// The r leading eigenpairs of a symmetric n x n matrix A (lda), r <= n,
+// r <= kTrdMaxRank, executed by group G:
+//   1. Householder tridiagonalization A = Q T Q^T (Golub & Van Loan,
+//      Algorithm 8.3.1), accumulating Q^T in Qt (n x n);
+//   2. the r largest eigenvalues of T by bisection on Sturm sequence sign
+//      counts (Golub & Van Loan, Section 8.4.1), one warp per eigenvalue and
+//      32 trial points per step (multisection: each step shrinks the
+//      bracket 33-fold), until the bracket is within a few ulps of ||T||;
+//   3. their eigenvectors x_j of T by inverse iteration (Golub & Van Loan,
+//      Section 8.2.2): three solves with T - lambda_j I, factored by
+//      Gaussian elimination with partial pivoting; eigenvalues closer than
+//      1e-3 ||T|| form a cluster, whose vectors one warp computes in order,
+//      orthogonalizing every iterate against the cluster's earlier ones;
+//   4. E = Q X (n x r, leading dimension lde), columns in descending order
+//      of the eigenvalues.
+// A is destroyed (its storage then holds X).  vec: trd_scratch_elems(n, r,
+// G::nwarps()) elements; sc: >= 4 elements; cl: >= 64 ints, all private to
+// the group.  Every step has a fixed order, so results are reproducible.
+template <class G, class S>
+__device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* vec, S* sc, int* cl) {
+  const int tid = G::rank(), nt = G::size(), lane = tid & 31, warp = tid >> 5, nw = G::nwarps();
+  S* d = vec;
+  S* e = d + n;
+  S* e2 = e + n;
+  S* v = e2 + n;
+  S* pv = v + n;
+  S* sv = pv + n;
+  S* lam = sv + n;
+  S* wsc = lam + 2 * r + 8;
+  // ---- Householder tridiagonalization, Q accumulated as Qt = Q^T --------
+  for (int idx = tid; idx < n * n; idx += nt) Qt[idx] = (idx / n == idx % n) ? S(1) : S(0);
+  G::sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m0 = k + 1;
+    if (warp == 0) {
+      S sig = 0;
+      for (int i = m0 + 1 + lane; i < n; i += 32) {
+        const S x = A[i * lda + k];
+        sig += x * x;
+      }
+      sig = warp_sum(sig);
+      const S alpha = A[m0 * lda + k];
+      S beta = 0, v1 = 1, mu = alpha;
+      if (sig > S(0)) {
+        mu = sqrt(alpha * alpha + sig);
+        v1 = alpha <= S(0) ? alpha - mu : -sig / (alpha + mu);
+        beta = S(2) * v1 * v1 / (sig + v1 * v1);
+        const S inv = S(1) / v1;
+        for (int i = m0 + lane; i < n; i += 32) v[i] = (i == m0) ? S(1) : A[i * lda + k] * inv;
+      }
+      if (lane == 0) {
+        sc[0] = beta;
+        e[k] = mu;
+        d[k] = A[k * lda + k];
+      }
+    }
+    G::sync();
+    const S beta = sc[0];
+    if (beta == S(0)) continue;
+    for (int i = m0 + tid; i < n; i += nt) {
+      S acc = 0;
+      for (int j = m0; j < n; ++j) acc += A[j * lda + i] * v[j];
+      pv[i] = beta * acc;
+    }
+    for (int i = tid; i < n; i += nt) {
+      S acc = 0;
+      for (int j = m0; j < n; ++j) acc += Qt[j * n + i] * v[j];
+      sv[i] = beta * acc;
+    }
+    G::sync();
+    S kk = 0;
+    for (int i = m0 + lane; i < n; i += 32) kk += pv[i] * v[i];
+    kk = warp_sum(kk) * (beta * S(0.5));
+    const int len = n - m0;
+    for (int idx = tid; idx < len * len; idx += nt) {
+      const int i = m0 + idx / len, j = m0 + idx % len;
+      const S wi = pv[i] - kk * v[i], wj = pv[j] - kk * v[j];
+      A[i * lda + j] -= v[i] * wj + wi * v[j];
+    }
+    for (int idx = tid; idx < len * n; idx += nt) {
+      const int j = m0 + idx / n, i = idx % n;
+      Qt[j * n + i] -= v[j] * sv[i];
+    }
+    G::sync();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(n - 2) * lda + (n - 2)];
+      e[n - 2] = A[(n - 1) * lda + (n - 2)];
+    }
+    d[n - 1] = A[(n - 1) * lda + (n - 1)];
+    // Gershgorin interval, pivmin
+    S gl = d[0], gu = d[0], emax = 0;
+    for (int i = 0; i < n; ++i) {
+      const S a = i > 0 ? fabs(e[i - 1]) : S(0), b = i + 1 < n ? fabs(e[i]) : S(0);
+      gl = fmin(gl, d[i] - a - b);
+      gu = fmax(gu, d[i] + a + b);
+      if (i + 1 < n) {
+        e2[i] = e[i] * e[i];
+        emax = fmax(emax, e2[i]);
+      }
+    }
+    const S w = gu - gl;
+    gl -= S(2) * Eps<S>::v() * w + Tiny<S>::v();
+    gu += S(2) * Eps<S>::v() * w + Tiny<S>::v();
+    sc[1] = gl;
+    sc[2] = gu;
+    sc[3] = Tiny<S>::v() * fmax(S(1), emax);
+  }
+  G::sync();
+  // ---- the r largest eigenvalues: multisection on Sturm counts ----------
+  {
+    const S gl = sc[1], gu = sc[2], pivmin = sc[3];
+    const S tnorm = fmax(fabs(gl), fabs(gu));
+    for (int j = warp; j < r; j += nw) {
+      const int m = n - 1 - j;  // ascending index of the j-th largest
+      S lo = gl, hi = gu;
+      for (int step = 0; step < (sizeof(S) == 8 ? 24 : 12); ++step) {
+        const S x = lo + (hi - lo) * (S)(lane + 1) * (S(1) / S(33));
+        int cnt = 0;
+        S q = d[0] - x;
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < S(0);
+        for (int i = 1; i < n; ++i) {
+          q = (d[i] - x) - qdiv(e2[i - 1], q);
+          if (fabs(q) < pivmin) q = -pivmin;
+          cnt += q < S(0);
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, cnt > m);
+        const int L = ball ? __ffs(ball) - 1 : 32;
+        const S nlo = L == 0 ? lo : lo + (hi - lo) * (S)L * (S(1) / S(33));
+        const S nhi = L == 32 ? hi : lo + (hi - lo) * (S)(L + 1) * (S(1) / S(33));
+        lo = nlo;
+        hi = nhi;
+        if (hi - lo <= S(4) * Eps<S>::v() * tnorm + pivmin) break;
+      }
+      if (lane == 0) lam[j] = S(0.5) * (lo + hi);
+    }
+  }
+  G::sync();
+  // ---- clusters of close eigenvalues (one warp each) ---------------------
+  if (tid == 0) {
+    const S ctol = S(1e-3) * fmax(fabs(sc[1]), fabs(sc[2]));
+    int nc = 0;
+    for (int j = 0; j < r; ++j)
+      if (j == 0 || lam[j - 1] - lam[j] > ctol) cl[nc++] = j;
+    cl[nc] = r;
+    cl[63] = nc;
+  }
+  G::sync();
+  const int nclus = cl[63];
+  const int nwv = nw < r ? nw : r;
+  S* X = A;  // r x n, row j = eigenvector of T for lam[j]
+  if (warp < nwv) {
+    S* xw = wsc + warp * 6 * n;
+    S* ua = xw + n;   // U diagonal
+    S* ub = ua + n;   // first superdiagonal
+    S* uc = ub + n;   // second superdiagonal
+    S* ml = uc + n;   // multipliers
+    S* pf = ml + n;   // pivot flags (1: rows swapped)
+    const S tnorm = fmax(fabs(sc[1]), fabs(sc[2]));
+    const S small = Eps<S>::v() * tnorm + Tiny<S>::v();
+    for (int c = warp; c < nclus; c += nwv) {
+      for (int j = cl[c]; j < cl[c + 1]; ++j) {
+        // separate equal eigenvalues inside a cluster slightly
+        S lj = lam[j];
+        if (j > cl[c]) lj = fmin(lj, lam[j - 1] - S(10) * Eps<S>::v() * tnorm);
+        if (lane == 0) {
+          // LU with partial pivoting of T - lj I (rows i, i+1)
+          S a = d[0] - lj, b = n > 1 ? e[0] : S(0);
+          for (int i = 0; i < n - 1; ++i) {
+            const S sub = e[i], nd = d[i + 1] - lj, ns = i + 2 < n ? e[i + 1] : S(0);
+            if (fabs(a) >= fabs(sub)) {
+              const S piv = fabs(a) < small ? (a < S(0) ? -small : small) : a;
+              const S mlt = sub / piv;
+              ua[i] = piv; ub[i] = b; uc[i] = 0; ml[i] = mlt; pf[i] = 0;
+              a = nd - mlt * b;
+              b = ns;
+            } else {
+              const S mlt = a / sub;
+              ua[i] = sub; ub[i] = nd; uc[i] = ns; ml[i] = mlt; pf[i] = 1;
+              a = b - mlt * nd;
+              b = -mlt * ns;
+            }
+          }
+          ua[n - 1] = fabs(a) < small ? (a < S(0) ? -small : small) : a;
+          ub[n - 1] = 0;
+          uc[n - 1] = 0;
+        }
+        __syncwarp();
+        // start vector: deterministic, all components non-zero
+        for (int i = lane; i < n; i += 32) xw[i] = S(1) + S(0.5) * (S)((i * 7 + j * 3) % 11) / S(11);
+        __syncwarp();
+        for (int itr = 0; itr < 3; ++itr) {
+          if (lane == 0) {
+            // forward: apply the row operations to the right-hand side
+            for (int i = 0; i < n - 1; ++i) {
+              if (pf[i] != S(0)) {
+                const S t = xw[i];
+                xw[i] = xw[i + 1];
+                xw[i + 1] = t - ml[i] * xw[i + 1];
+              } else {
+                xw[i + 1] -= ml[i] * xw[i];
+              }
+            }
+            // back substitution with U (diagonal ua, superdiagonals ub, uc)
+            for (int i = n - 1; i >= 0; --i) {
+              S t = xw[i];
+              if (i + 1 < n) t -= ub[i] * xw[i + 1];
+              if (i + 2 < n) t -= uc[i] * xw[i + 2];
+              xw[i] = t / ua[i];
+            }
+          }
+          __syncwarp();
+          // orthogonalize against the cluster's earlier vectors, normalize
+          for (int jj = cl[c]; jj < j; ++jj) {
+            S dot = 0;
+            for (int i = lane; i < n; i += 32) dot += X[jj * n + i] * xw[i];
+            dot = warp_sum(dot);
+            for (int i = lane; i < n; i += 32) xw[i] -= dot * X[jj * n + i];
+            __syncwarp();
+          }
+          S nr = 0;
+          for (int i = lane; i < n; i += 32) nr += xw[i] * xw[i];
+          nr = warp_sum(nr);
+          const S inv = nr > S(0) ? S(1) / sqrt(nr) : S(0);
+          for (int i = lane; i < n; i += 32) xw[i] *= inv;
+          __syncwarp();
+        }
+        for (int i = lane; i < n; i += 32) X[j * n + i] = xw[i];
+        __syncwarp();
+      }
+    }
+  }
+  G::sync();
+  // ---- back-transformation E = Q X^T (n x r) ------------------------------
+  for (int idx = tid; idx < n * r; idx += nt) {
+    const int i = idx / r, j = idx % r;
+    S acc = 0;
+    for (int k = 0; k < n; ++k) acc += Qt[k * n + i] * X[j * n + k];
+    E[i * lde + j] = acc;
+  }
+  G::sync();
+}
+
+
 // E (n x r, leading dimension lde) <- the eigenvectors (columns of V, n x n)
 // of the r largest eigenvalues w, in descending order (ties by index).
 template <class G, class S>

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "tk_device.cuh"
 #include "tk_internal.h"
 
 namespace {
@@ -262,6 +263,10 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   tot += round32(rprod);
   // T of the warm start, and the eig scratch if it spills out of shared memory
   tot += 3 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
+  // vectors of the tridiagonal eigensolver (a group has at most 32 warps)
+  int rmax = 1;
+  for (int n = 0; n < p; ++n) rmax = std::max(rmax, r[n]);
+  tot += round32(tk::trd_scratch_elems((int)neig, rmax, 32));
   return tot + 256;
 }
 
@@ -314,8 +319,15 @@ TkLeafLayout leaf_layout(const tk_tree* t, int nsm, int64_t* per_cluster) {
   ly.b0 = take(chain);
   ly.b1 = take(chain);
   ly.T = take(neig * neig);
+  {
+    int rmx = 1;
+    for (int n = 0; n < p; ++n) rmx = std::max<int>(rmx, (int)r[n]);
+    ly.trd = take(tk::trd_scratch_elems((int)neig, rmx, TK_NT / 32));
+  }
   ly.nsm = nsm;
   ly.neig = (int)neig;
+  ly.rmax = 1;
+  for (int n = 0; n < p; ++n) ly.rmax = std::max<int>(ly.rmax, (int)r[n]);
   ly.half = neig / 2 + 2;
   ly.eig_in_smem = neig <= nsm;
   if (!ly.eig_in_smem) {
@@ -426,7 +438,7 @@ int run_leaves(tk_tree* t, const void* raw, int64_t block_stride, int64_t first,
   if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
   int64_t per = 0;
   const TkLeafLayout probe = leaf_layout(t, t->nsm_leaf, &per);
-  int maxc = tk_leaf_max_clusters(t->cfg.dtype, tk_leaf_smem_bytes(t->cfg.dtype, probe.nsm, probe.neig));
+  int maxc = tk_leaf_max_clusters(t->cfg.dtype, tk_leaf_smem_bytes(t->cfg.dtype, probe.nsm, probe.neig, probe.rmax));
   if (maxc < 1) maxc = 1;
   const int ncl = std::min(njobs, maxc);
   TkLeafLayout ly{};

@@ -56,7 +56,7 @@ template <class S> struct StitchCtx {
   int qmax[TK_MAXP];
   HitRec* hits;       // the job's hit records (shared-memory copy when it fits)
   S *phi[TK_MAXP], *tau[TK_MAXP], *R[TK_MAXP], *E[TK_MAXP], *Vs[TK_MAXP];
-  S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs;
+  S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs, *trdv;
   int* pq;
   int neig;           // largest eig order of the job
   int smem_used;      // bytes of the shared arena in use
@@ -68,6 +68,7 @@ template <class S> struct WarpSm {
   StitchCtx<S> ctx;
   S red[40];
   S sc[4];
+  int cl[64];
   int flag;
   int job;
   int nsw;
@@ -320,6 +321,11 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     cx.cs = take(2 * (neig / 2 + 2));
     cx.pq = reinterpret_cast<int*>(take_bytes(sizeof(int) * (size_t)(neig / 2 + 2)));
     cx.T = take((int64_t)neig * neig);
+    {
+      int rmx = 1;
+      for (int n = 0; n < p; ++n) rmx = cx.ro[n] > rmx ? cx.ro[n] : rmx;
+      cx.trdv = take(trd_scratch_elems(neig, rmx, G::nwarps()));
+    }
     // chain buffers: every intermediate has, per mode, at most max(q_max, ro, nr0) (or c_n) entries
     int64_t tb = 0;
     for (int n = 0; n < p; ++n) {
@@ -403,20 +409,27 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   for (int n = 0; n < TK_MAXP; ++n) have_v[n] = false;
   int sweeps = 0;
   long long eig_cyc = 0, qr_cyc = 0;
-  // eigenvectors of the order-nsz matrix in A, warm-started from the mode's previous basis
-  auto eig = [&](int mode_n, int nsz) {
+  // leading ro[mode_n] eigenvectors of the order-nsz matrix in A, written to
+  // Edst (leading dimension lde): the tridiagonal method from order
+  // kTrdMinOrder on, else Jacobi warm-started from the mode's previous basis
+  auto eig = [&](int mode_n, int nsz, S* Edst, int lde) {
     const long long c0 = clock64();
     const int rkeep = cx.ro[mode_n];
-    S* Vs = cx.Vs[mode_n];
-    const bool warm = have_v[mode_n];
-    if (warm) {
-      for (int i = lane; i < nsz * nsz; i += nt) V[i] = Vs[i];
+    if (nsz >= kTrdMinOrder && rkeep <= kTrdMaxRank) {
+      trd_eig<G, S>(nsz, rkeep, A, nsz, V, Edst, lde, cx.trdv, sm.sc, sm.cl);
+    } else {
+      S* Vs = cx.Vs[mode_n];
+      const bool warm = have_v[mode_n];
+      if (warm) {
+        for (int i = lane; i < nsz * nsz; i += nt) V[i] = Vs[i];
+        G::sync();
+      }
+      sweeps += jacobi_eig<G, S>(nsz, rkeep, A, V, T, warm, wv, js, maxsw);
+      for (int i = lane; i < nsz * nsz; i += nt) Vs[i] = V[i];
       G::sync();
+      have_v[mode_n] = true;
+      select_top<G, S>(nsz, wv, V, rkeep, Edst, lde);
     }
-    sweeps += jacobi_eig<G, S>(nsz, rkeep, A, V, T, warm, wv, js, maxsw);
-    for (int i = lane; i < nsz * nsz; i += nt) Vs[i] = V[i];
-    G::sync();
-    have_v[mode_n] = true;
     eig_cyc += clock64() - c0;
   };
   int dims[TK_MAXP];
@@ -521,8 +534,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       dims[n] = cn;
       mode_gram<G, S>(b0, dims, p, n, A, cn, true);
     }
-    eig(n, cn);
-    select_top<G, S>(cn, wv, V, cx.ro[n], cx.E[n], cx.ro[n]);
+    eig(n, cn, cx.E[n], cx.ro[n]);
   }
 
   // ---- Algorithm 2 iterations --------------------------------------------
@@ -558,8 +570,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       dims[0] = c0;
       for (int m = 1; m < p; ++m) dims[m] = ro[m];
       mode_gram<G, S>(K, dims, p, 0, A, c0, false);
-      eig(0, c0);
-      select_top<G, S>(c0, wv, V, ro[0], C, ro[0]);
+      eig(0, c0, C, ro[0]);
     }
     // non-temporal modes, Eq. (stitch-nontemp-3) in coefficient space
     for (int n = 1; n < p; ++n) {
@@ -586,8 +597,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       for (int m = 0; m < p; ++m) dims[m] = ro[m];
       dims[n] = cn;
       mode_gram<G, S>(N, dims, p, n, A, cn, false);
-      eig(n, cn);
-      select_top<G, S>(cn, wv, V, ro[n], cx.E[n], ro[n]);
+      eig(n, cn, cx.E[n], ro[n]);
     }
     // core: G = N_p x_p E_p^T (Algorithm 2's last step) and the stop test
     {

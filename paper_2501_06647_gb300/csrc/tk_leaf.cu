@@ -25,8 +25,9 @@ namespace tk {
 
 namespace {
 
-constexpr int kHdr = 512;  // bytes of the shared header
+constexpr int kHdr = 1024;  // bytes of the shared header
 constexpr int kKC = 32;    // Gram columns staged in shared memory at a time
+constexpr int kStage = 16 * TK_NT;  // elements of the staging buffer of a contraction
 
 template <class S> struct LeafSm {
   S red[40];
@@ -35,6 +36,7 @@ template <class S> struct LeafSm {
   int nsw;
   S thr;
   S xn2;
+  int cl[64];
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -90,15 +92,48 @@ __device__ __forceinline__ int64_t prod64(const int* d, int a, int b) {
 // C-order tensor seen as (outer, D, inner): x_c[a] = X[(o D + a) inner + i],
 // c = o inner + i.  One CTA: kKC columns at a time are staged in shared
 // memory (`tile`, kKC * round4(D) elements, 16-byte aligned) and every thread
-// accumulates 4x4 blocks of the upper triangle, mirrored on output.  Every
-// entry sums its columns in increasing order.
+// accumulates 4x4 blocks of the upper triangle, mirrored on output.  The
+// loads of the next kKC columns are issued into registers before the current
+// ones are used, so their latency overlaps the arithmetic.  Every entry sums
+// its columns in increasing order.
 template <class S>
 __device__ void gram_cols(const S* X, int D, int64_t inner, int64_t c0, int64_t c1, S* A, int lda, S* tile) {
   constexpr int MT = 2;
+  // staged elements per thread and tile (the register prefetch is used for
+  // float only: in double it would spill, and the double path is not hot)
+  constexpr int PF = sizeof(S) == 4 ? 20 : 1;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int ld = (D + 3) & ~3;
   const int nb4 = ld / 4;
   const int ntile = nb4 * (nb4 + 1) / 2;
+  const int per = (kKC * ld + nt - 1) / nt;  // staged elements per thread
+  const bool fits = sizeof(S) == 4 && per <= PF;
+  // staging map (fixed for every tile): element u of this thread is (kk[u], a[u])
+  int skk[PF], sa[PF];
+#pragma unroll
+  for (int u = 0; u < PF; ++u) {
+    if (inner == 1) {
+      const int e = tid + u * nt;
+      skk[u] = e / ld;
+      sa[u] = e - skk[u] * ld;
+    } else {
+      skk[u] = lane;
+      sa[u] = warp + u * nw;
+    }
+  }
+  auto fetch = [&](int64_t c, int kc, S* v) {
+    if (inner == 1) {
+#pragma unroll
+      for (int u = 0; u < PF; ++u)
+        v[u] = (u < per && skk[u] < kc && sa[u] < D) ? X[(c + skk[u]) * D + sa[u]] : S(0);
+    } else {
+      const int64_t col = c + lane;
+      const int64_t o = col / inner, i = col - o * inner;
+      const S* xp = X + o * D * inner + i;
+#pragma unroll
+      for (int u = 0; u < PF; ++u) v[u] = (u < per && lane < kc && sa[u] < D) ? xp[(int64_t)sa[u] * inner] : S(0);
+    }
+  };
   for (int pass0 = 0; pass0 < ntile; pass0 += nt * MT) {
     int I[MT], J[MT];
     bool act[MT];
@@ -122,10 +157,16 @@ __device__ void gram_cols(const S* X, int D, int64_t inner, int64_t c0, int64_t 
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[u][x][y] = S(0);
+    S v[PF];
+    if (fits && c0 < c1) fetch(c0, (int)((c1 - c0) < kKC ? (c1 - c0) : kKC), v);
     for (int64_t c = c0; c < c1; c += kKC) {
       const int kc = (int)((c1 - c) < kKC ? (c1 - c) : kKC);
       __syncthreads();  // the previous tile has been consumed
-      if (inner == 1) {  // a column is D contiguous elements
+      if (fits) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+          if (u < per && skk[u] < kKC && sa[u] < ld) tile[skk[u] * ld + sa[u]] = v[u];
+      } else if (inner == 1) {  // a column is D contiguous elements
         for (int kk = warp; kk < kc; kk += nw) {
           const S* xp = X + (c + kk) * D;
           for (int a = lane; a < ld; a += 32) tile[kk * ld + a] = a < D ? xp[a] : S(0);
@@ -139,6 +180,7 @@ __device__ void gram_cols(const S* X, int D, int64_t inner, int64_t c0, int64_t 
         }
       }
       __syncthreads();
+      if (fits && c + kKC < c1) fetch(c + kKC, (int)((c1 - c - kKC) < kKC ? (c1 - c - kKC) : kKC), v);
       for (int kk = 0; kk < kc; ++kk) {
         const S* row = tile + kk * ld;
 #pragma unroll
@@ -172,13 +214,78 @@ __device__ void gram_cols(const S* X, int D, int64_t inner, int64_t c0, int64_t 
   __syncthreads();
 }
 
+// Y = X x_m M^T... for a C-order tensor X seen as (outer, dm, inner) whose
+// blocks X_o (dm x inner) are contiguous and hold at most kStage elements:
+// Y_o (a x inner) = U^T X_o with U (dm x a, row-major) the factor, i.e. the
+// mode-m product with U^T.  U is copied to shared memory (`us`, dm x round4(a))
+// and X streams through `stage` (kStage elements) in chunks of whole blocks;
+// the next chunk's loads are issued into registers before the current chunk
+// is used.  Each output sums over j = 0..dm-1 in order.
+template <class S>
+__device__ void ttm_staged(const S* X, int64_t outer, int dm, int inner, const S* U, int a, S* Y, S* stage, S* us) {
+  constexpr int PF = kStage / TK_NT;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int a4 = (a + 3) & ~3;
+  for (int e = tid; e < dm * a4; e += nt) {
+    const int j = e / a4, al = e - j * a4;
+    us[e] = al < a ? U[j * a + al] : S(0);
+  }
+  const int blk = dm * inner;
+  const int ob = kStage / blk;  // blocks per chunk
+  const int64_t nchunk = (outer + ob - 1) / ob;
+  const int nch = a4 / 4;
+  auto fetch = [&](int64_t ch, S* v) {
+    const int64_t o0 = ch * ob;
+    const int64_t cnt = ((outer - o0) < ob ? (outer - o0) : ob) * blk;
+    const S* xp = X + o0 * blk;
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int e = tid + u * nt;
+      v[u] = e < cnt ? xp[e] : S(0);
+    }
+  };
+  S v[PF];
+  if (nchunk > 0) fetch(0, v);
+  for (int64_t ch = 0; ch < nchunk; ++ch) {
+    const int64_t o0 = ch * ob;
+    const int nob = (int)((outer - o0) < ob ? (outer - o0) : ob);
+    __syncthreads();  // the stage (and, first time, us) is free / ready
+#pragma unroll
+    for (int u = 0; u < PF; ++u) stage[tid + u * nt] = v[u];
+    __syncthreads();
+    if (ch + 1 < nchunk) fetch(ch + 1, v);
+    // items (ob, c4, i), i fastest
+    const int items = nob * nch * inner;
+    for (int it = tid; it < items; it += nt) {
+      const int i = it % inner;
+      const int t = it / inner;
+      const int c4 = t % nch, b = t / nch;
+      const S* xs = stage + b * blk + i;
+      const S* ms = us + 4 * c4;
+      S acc[4] = {S(0), S(0), S(0), S(0)};
+      for (int j = 0; j < dm; ++j) {
+        const S x = xs[j * inner];
+        S mv[4];
+        ld4(ms + j * a4, mv);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += mv[c] * x;
+      }
+      S* yp = Y + ((o0 + b) * a + 4 * c4) * inner + i;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (4 * c4 + c < a) yp[c * inner] = acc[c];
+    }
+  }
+  __syncthreads();
+}
+
 // Rows [s0, s1) of mat_n(Y_n), Y_n = X x_{m != n} U_m^T (modes contracted
 // from the last to the first), written to Y (D_n x Rn, row-major).  The slab
 // X[..., s0:s1, ...] is first gathered into a contiguous buffer (mode 0's slab
 // is contiguous already), then contracted with the block's TTM routine.
 template <class S>
 __device__ void slab_rows(const S* X, const int* xd, const int* rl, int p, int n, int s0, int s1, const S* const* U,
-                          S* slab, S* b0, S* b1, S* Y, int64_t Rn) {
+                          S* slab, S* b0, S* b1, S* Y, int64_t Rn, S* stage, S* us) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ds = s1 - s0;
   int dims[TK_MAXP];
@@ -190,18 +297,30 @@ __device__ void slab_rows(const S* X, const int* xd, const int* rl, int p, int n
     src = X + (int64_t)s0 * inner;
   } else {
     // for each outer index o the slab's rows are ds * inner contiguous elements
-    // of X; element e = o * len + off is walked with carries (no division)
+    // of X; element e = o * len + off is walked with carries (no division),
+    // kGather elements per thread at a time so that their loads overlap
+    constexpr int kGather = 16;
     const int64_t len = (int64_t)ds * inner, tot = outer * len;
     const int64_t dO = nt / len, dOff = nt - dO * len;
     int64_t o = tid / len, off = tid - (tid / len) * len;
-    for (int64_t e = tid; e < tot; e += nt) {
-      slab[e] = X[(o * xd[n] + s0) * inner + off];
-      off += dOff;
-      o += dO;
-      if (off >= len) {
-        off -= len;
-        ++o;
+    for (int64_t e0 = tid; e0 < tot; e0 += (int64_t)kGather * nt) {
+      S v[kGather];
+      int64_t oo = o, of = off;
+#pragma unroll
+      for (int u = 0; u < kGather; ++u) {
+        v[u] = (e0 + (int64_t)u * nt < tot) ? X[(oo * xd[n] + s0) * inner + of] : S(0);
+        of += dOff;
+        oo += dO;
+        if (of >= len) {
+          of -= len;
+          ++oo;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < kGather; ++u)
+        if (e0 + (int64_t)u * nt < tot) slab[e0 + (int64_t)u * nt] = v[u];
+      o = oo;
+      off = of;
     }
     __syncthreads();
     src = slab;
@@ -209,7 +328,11 @@ __device__ void slab_rows(const S* X, const int* xd, const int* rl, int p, int n
   S* dst = b0;
   for (int m = p - 1; m >= 0; --m) {
     if (m == n) continue;
-    ttm<BlockGroup, S>(src, dims, p, m, U[m], 1, rl[m], rl[m], dst, false);
+    const int64_t in = prod64(dims, m + 1, p);
+    if ((int64_t)dims[m] * in <= kStage)
+      ttm_staged<S>(src, prod64(dims, 0, m), dims[m], (int)in, U[m], rl[m], dst, stage, us);
+    else
+      ttm<BlockGroup, S>(src, dims, p, m, U[m], 1, rl[m], rl[m], dst, false);
     dims[m] = rl[m];
     src = dst;
     dst = (dst == b0) ? b1 : b0;
@@ -251,6 +374,10 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
   S* sV = reinterpret_cast<S*>(smem_raw + off);
   off += align16(sizeof(S) * (size_t)nsm * nsm);
   S* tile = reinterpret_cast<S*>(smem_raw + off);
+  off += align16(sizeof(S) * (size_t)kKC * ((ly.neig + 3) & ~3));
+  S* stage = reinterpret_cast<S*>(smem_raw + off);
+  off += align16(sizeof(S) * (size_t)kStage);
+  S* us = reinterpret_cast<S*>(smem_raw + off);
 
   S* wc = reinterpret_cast<S*>(wsd.base) + (int64_t)cid * wsd.per_cta;  // the cluster's chunk
   S* wt = wc + ly.cta + (int64_t)crank * ly.cta_stride;                 // this CTA's part
@@ -323,10 +450,14 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
         A[i] = a;
       }
       __syncthreads();
-      jacobi_eig<BG, S>(D, rl[n], A, V, T, false, ew, js, maxsw);
-      select_top<BG, S>(D, ew, V, rl[n], wc + ly.U[n], rl[n]);
-      for (int i = tid; i < DD; i += nt) wc[ly.Vs[n] + i] = V[i];
-      __syncthreads();
+      if (D >= kTrdMinOrder && rl[n] <= kTrdMaxRank) {
+        trd_eig<BG, S>(D, rl[n], A, D, V, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
+      } else {
+        jacobi_eig<BG, S>(D, rl[n], A, V, T, false, ew, js, maxsw);
+        select_top<BG, S>(D, ew, V, rl[n], wc + ly.U[n], rl[n]);
+        for (int i = tid; i < DD; i += nt) wc[ly.Vs[n] + i] = V[i];
+        __syncthreads();
+      }
     }
     if (crank == 0 && tid == 0) {
       S a = 0;
@@ -346,19 +477,26 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
           if (m != n) Rn *= rl[m];
         const int s0 = (int)((int64_t)dn * crank / TK_LEAF_CL);
         const int s1 = (int)((int64_t)dn * (crank + 1) / TK_LEAF_CL);
-        if (s1 > s0) slab_rows<S>(X, xd, rl, p, n, s0, s1, U, wt + ly.slab, wt + ly.b0, wt + ly.b1, wc + ly.Y, Rn);
+        if (s1 > s0)
+          slab_rows<S>(X, xd, rl, p, n, s0, s1, U, wt + ly.slab, wt + ly.b0, wt + ly.b1, wc + ly.Y, Rn, stage, us);
         cluster_barrier();
         if (crank == 0) {
           const S* Y = wc + ly.Y;
           gram_cols<S>(Y, dn, Rn, 0, Rn, A, dn, tile);
-          const bool warm = n > 0 || it > 1;
-          if (warm) {
-            for (int i = tid; i < dn * dn; i += nt) V[i] = wc[ly.Vs[n] + i];
-            __syncthreads();
+          if (dn >= kTrdMinOrder && rl[n] <= kTrdMaxRank) {
+            trd_eig<BG, S>(dn, rl[n], A, dn, V, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
+          } else {
+            // Jacobi, warm-started from the mode's previous basis (the HOSVD
+            // start's for n >= 2 in the first iteration)
+            const bool warm = n > 0 || it > 1;
+            if (warm) {
+              for (int i = tid; i < dn * dn; i += nt) V[i] = wc[ly.Vs[n] + i];
+              __syncthreads();
+            }
+            jacobi_eig<BG, S>(dn, rl[n], A, V, T, warm, ew, js, maxsw);
+            select_top<BG, S>(dn, ew, V, rl[n], wc + ly.U[n], rl[n]);
+            for (int i = tid; i < dn * dn; i += nt) wc[ly.Vs[n] + i] = V[i];
           }
-          jacobi_eig<BG, S>(dn, rl[n], A, V, T, warm, ew, js, maxsw);
-          select_top<BG, S>(dn, ew, V, rl[n], wc + ly.U[n], rl[n]);
-          for (int i = tid; i < dn * dn; i += nt) wc[ly.Vs[n] + i] = V[i];
           if (n == p - 1) {
             // core: G = fold_p(U_p^T mat_p(Y_p)), G[o * r_p + a] = sum_d U_p[d, a] Y[d, o]
             __syncthreads();
@@ -419,13 +557,15 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
 
 using namespace tk;
 
-size_t tk_leaf_smem_bytes(int dtype, int nsm, int neig) {
+size_t tk_leaf_smem_bytes(int dtype, int nsm, int neig, int rmax) {
   const size_t es = dtype == TK_F64 ? 8 : 4;
   const int half_cap = nsm / 2 + 2;
   size_t b = kHdr + align16(half_cap * sizeof(int));
   b += align16(es * (2 * half_cap + nsm + 2));
   b += 2 * align16(es * (size_t)nsm * nsm);
-  b += es * (size_t)kKC * ((neig + 3) & ~3);
+  b += align16(es * (size_t)kKC * ((neig + 3) & ~3));
+  b += align16(es * (size_t)kStage);
+  b += es * (size_t)neig * ((rmax + 3) & ~3);
   return b;
 }
 
@@ -450,7 +590,7 @@ int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t blo
                    int njobs, int ell, const TkWorkspace& ws, const TkLeafLayout& ly, int nclusters,
                    cudaStream_t stream) {
   if (njobs <= 0) return TK_OK;
-  const size_t smem = tk_leaf_smem_bytes(dtype, ly.nsm, ly.neig);
+  const size_t smem = tk_leaf_smem_bytes(dtype, ly.nsm, ly.neig, ly.rmax);
   const dim3 grid(TK_LEAF_CL * nclusters);
   if (dtype == TK_F64) {
     if (cudaFuncSetAttribute(leaf_fn<double>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
