@@ -195,6 +195,52 @@ __device__ void gemm(int M, int N, int K, const S* A, int ars, int acs, const S*
   G::sync();
 }
 
+// Applies the reflector H = I - tau v v^T, v = (1, A[r0+1..m-1][j]) (column
+// j of A below row r0), to columns [0, nc) of B (rows r0..m-1, leading
+// dimension ldb): w_c = tau (B[r0][c] + sum_{i>r0} v_i B[i][c]), then
+// B[r0][c] -= w_c and B[i][c] -= w_c v_i.  Every thread of the CTA takes a
+// share of the rows and accumulates the dot products of up to 16 columns at
+// once; one reduction then serves all of them.  For tall matrices (m much
+// larger than the CTA), where one warp per column would walk the rows alone.
+// wbuf: >= 16 * (nwarps + 1) elements of shared scratch.
+template <class S>
+__device__ void reflect_cols(const S* A, int lda, int j, int r0, int m, S tau, S* B, int64_t ldb, int nc, S* wbuf) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  S* wfin = wbuf + 16 * nw;
+  for (int c0 = 0; c0 < nc; c0 += 16) {
+    const int cw = nc - c0 < 16 ? nc - c0 : 16;
+    S acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = S(0);
+    for (int i = r0 + 1 + tid; i < m; i += nt) {
+      const S vi = A[(int64_t)i * lda + j];
+      const S* bp = B + i * ldb + c0;
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < cw) acc[c] += vi * bp[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = warp_sum(acc[c]);
+    if (lane == 0)
+      for (int c = 0; c < cw; ++c) wbuf[warp * 16 + c] = acc[c];
+    __syncthreads();
+    if (tid < cw) {
+      S w = B[r0 * ldb + c0 + tid];
+      for (int q = 0; q < nw; ++q) w += wbuf[q * 16 + tid];
+      w *= tau;
+      wfin[tid] = w;
+      B[r0 * ldb + c0 + tid] -= w;
+    }
+    __syncthreads();
+    for (int i = r0 + 1 + tid; i < m; i += nt) {
+      const S vi = A[(int64_t)i * lda + j];
+      S* bp = B + i * ldb + c0;
+      for (int c = 0; c < cw; ++c) bp[c] -= wfin[c] * vi;
+    }
+    __syncthreads();
+  }
+}
+
 // Householder QR of the row-major m x n matrix A (leading dimension lda), in
 // place (Golub & Van Loan, Algorithm 5.2.1, with LAPACK's dlarfg convention):
 // on return the upper triangle holds R (min(m,n) x n) and the part below the
@@ -202,9 +248,44 @@ __device__ void gemm(int M, int N, int K, const S* A, int ars, int acs, const S*
 // H_j = I - tau_j v_j v_j^T and A_in = H_0 H_1 ... H_{k-1} R.  tau: min(m,n).
 // sc: >= 3 S of group-private shared scratch.
 template <class G, class S>
-__device__ void householder_qr(S* A, int m, int n, int lda, S* tau, S* sc) {
+__device__ void householder_qr(S* A, int m, int n, int lda, S* tau, S* sc, S* red = nullptr, S* wbuf = nullptr) {
   const int kmax = m < n ? m : n;
   const int lane = G::rank() & 31, warp = G::rank() >> 5, nw = G::nwarps();
+  if (wbuf && G::nwarps() > 1 && m >= 2 * G::size()) {
+    // tall: every thread takes part in every reduction (reflect_cols)
+    for (int j = 0; j < kmax; ++j) {
+      S s = 0;
+      for (int i = j + 1 + G::rank(); i < m; i += G::size()) {
+        const S v = A[(int64_t)i * lda + j];
+        s += v * v;
+      }
+      s = G::template sum<S>(s, red);
+      if (G::rank() == 0) {
+        const S x0 = A[(int64_t)j * lda + j];
+        S t = 0, beta = x0, scale = 0;
+        if (s != S(0)) {
+          const S nrm = sqrt(x0 * x0 + s);
+          beta = x0 >= S(0) ? -nrm : nrm;
+          t = (beta - x0) / beta;
+          scale = S(1) / (x0 - beta);
+        }
+        sc[0] = t;
+        sc[1] = scale;
+        sc[2] = beta;
+        tau[j] = t;
+      }
+      G::sync();
+      const S t = sc[0], scale = sc[1], beta = sc[2];
+      if (t != S(0)) {
+        for (int i = j + 1 + G::rank(); i < m; i += G::size()) A[(int64_t)i * lda + j] *= scale;
+        G::sync();
+        reflect_cols<S>(A, lda, j, j, m, t, A + j + 1, lda, n - j - 1, wbuf);
+      }
+      if (G::rank() == 0) A[(int64_t)j * lda + j] = beta;
+      G::sync();
+    }
+    return;
+  }
   for (int j = 0; j < kmax; ++j) {
     if (warp == 0) {
       S s = 0;
@@ -254,8 +335,13 @@ __device__ void householder_qr(S* A, int m, int n, int lda, S* tau, S* sc) {
 // first rows and zeros below before the call.
 template <class G, class S>
 __device__ void householder_apply_q(const S* A, int m, int kmax, int lda, const S* tau, S* Y, int ncols,
-                                    int64_t ldy) {
+                                    int64_t ldy, S* wbuf = nullptr) {
   const int lane = G::rank() & 31, warp = G::rank() >> 5, nw = G::nwarps();
+  if (wbuf && G::nwarps() > 1 && m >= 2 * G::size()) {
+    for (int j = kmax - 1; j >= 0; --j)
+      if (tau[j] != S(0)) reflect_cols<S>(A, lda, j, j, m, tau[j], Y, ldy, ncols, wbuf);
+    return;
+  }
   for (int j = kmax - 1; j >= 0; --j) {
     const S t = tau[j];
     if (t == S(0)) continue;
@@ -543,7 +629,7 @@ __host__ __device__ inline int trd_scratch_elems(int n, int r, int nw) {
 //      32 trial points per step (multisection: each step shrinks the
 //      bracket 33-fold), until the bracket is within a few ulps of ||T||;
 //   3. their eigenvectors x_j of T by inverse iteration (Golub & Van Loan,
-//      Section 8.2.2): three solves with T - lambda_j I, factored by
+//      Section 8.2.2): two solves with T - lambda_j I, factored by
 //      Gaussian elimination with partial pivoting; eigenvalues closer than
 //      1e-3 ||T|| form a cluster, whose vectors one warp computes in order,
 //      orthogonalizing every iterate against the cluster's earlier ones;
@@ -593,29 +679,33 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
     G::sync();
     const S beta = sc[0];
     if (beta == S(0)) continue;
-    for (int i = m0 + tid; i < n; i += nt) {
-      S acc = 0;
-      for (int j = m0; j < n; ++j) acc += A[j * lda + i] * v[j];
-      pv[i] = beta * acc;
-    }
-    for (int i = tid; i < n; i += nt) {
-      S acc = 0;
-      for (int j = m0; j < n; ++j) acc += Qt[j * n + i] * v[j];
-      sv[i] = beta * acc;
+    // p = beta A v (A symmetric: thread i walks column i) and s = beta Q v
+    // (Q^T stored: thread i walks column i of Qt), by the two halves of the group
+    {
+      const int half = nt >> 1;
+      const bool second = tid >= half;
+      const int t0 = second ? tid - half : tid;
+      const S* M = second ? Qt : A;
+      const int ldm = second ? n : lda;
+      S* outv = second ? sv : pv;
+      for (int i = (second ? 0 : m0) + t0; i < n; i += half) {
+        S acc = 0;
+        for (int j = m0; j < n; ++j) acc += M[j * ldm + i] * v[j];
+        outv[i] = beta * acc;
+      }
     }
     G::sync();
     S kk = 0;
     for (int i = m0 + lane; i < n; i += 32) kk += pv[i] * v[i];
     kk = warp_sum(kk) * (beta * S(0.5));
-    const int len = n - m0;
-    for (int idx = tid; idx < len * len; idx += nt) {
-      const int i = m0 + idx / len, j = m0 + idx % len;
-      const S wi = pv[i] - kk * v[i], wj = pv[j] - kk * v[j];
-      A[i * lda + j] -= v[i] * wj + wi * v[j];
+    // A <- A - v w^T - w v^T with w = p - K v; Q <- Q - s v^T (rows by warps)
+    for (int i = m0 + warp; i < n; i += nw) {
+      const S vi = v[i], wi = pv[i] - kk * vi;
+      for (int j = m0 + lane; j < n; j += 32) A[i * lda + j] -= vi * (pv[j] - kk * v[j]) + wi * v[j];
     }
-    for (int idx = tid; idx < len * n; idx += nt) {
-      const int j = m0 + idx / n, i = idx % n;
-      Qt[j * n + i] -= v[j] * sv[i];
+    for (int j = m0 + warp; j < n; j += nw) {
+      const S vj = v[j];
+      for (int i = lane; i < n; i += 32) Qt[j * n + i] -= vj * sv[i];
     }
     G::sync();
   }
@@ -689,7 +779,7 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
   S* X = A;  // r x n, row j = eigenvector of T for lam[j]
   if (warp < nwv) {
     S* xw = wsc + warp * 6 * n;
-    S* ua = xw + n;   // U diagonal
+    S* ua = xw + n;   // reciprocals of U's diagonal
     S* ub = ua + n;   // first superdiagonal
     S* uc = ub + n;   // second superdiagonal
     S* ml = uc + n;   // multipliers
@@ -708,18 +798,19 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
             const S sub = e[i], nd = d[i + 1] - lj, ns = i + 2 < n ? e[i + 1] : S(0);
             if (fabs(a) >= fabs(sub)) {
               const S piv = fabs(a) < small ? (a < S(0) ? -small : small) : a;
-              const S mlt = sub / piv;
-              ua[i] = piv; ub[i] = b; uc[i] = 0; ml[i] = mlt; pf[i] = 0;
+              const S rp = S(1) / piv;
+              const S mlt = sub * rp;
+              ua[i] = rp; ub[i] = b; uc[i] = 0; ml[i] = mlt; pf[i] = 0;
               a = nd - mlt * b;
               b = ns;
             } else {
               const S mlt = a / sub;
-              ua[i] = sub; ub[i] = nd; uc[i] = ns; ml[i] = mlt; pf[i] = 1;
+              ua[i] = S(1) / sub; ub[i] = nd; uc[i] = ns; ml[i] = mlt; pf[i] = 1;
               a = b - mlt * nd;
               b = -mlt * ns;
             }
           }
-          ua[n - 1] = fabs(a) < small ? (a < S(0) ? -small : small) : a;
+          ua[n - 1] = S(1) / (fabs(a) < small ? (a < S(0) ? -small : small) : a);
           ub[n - 1] = 0;
           uc[n - 1] = 0;
         }
@@ -727,7 +818,7 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
         // start vector: deterministic, all components non-zero
         for (int i = lane; i < n; i += 32) xw[i] = S(1) + S(0.5) * (S)((i * 7 + j * 3) % 11) / S(11);
         __syncwarp();
-        for (int itr = 0; itr < 3; ++itr) {
+        for (int itr = 0; itr < 2; ++itr) {
           if (lane == 0) {
             // forward: apply the row operations to the right-hand side
             for (int i = 0; i < n - 1; ++i) {
@@ -744,7 +835,7 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
               S t = xw[i];
               if (i + 1 < n) t -= ub[i] * xw[i + 1];
               if (i + 2 < n) t -= uc[i] * xw[i + 2];
-              xw[i] = t / ua[i];
+              xw[i] = t * ua[i];
             }
           }
           __syncwarp();

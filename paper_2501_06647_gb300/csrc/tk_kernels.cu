@@ -69,6 +69,7 @@ template <class S> struct WarpSm {
   S red[40];
   S sc[4];
   int cl[64];
+  S wbuf[16 * 33];  // reflector dot products (reflect_cols), up to 32 warps
   int flag;
   int job;
   int nsw;
@@ -320,7 +321,14 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     cx.w = take(neig + 2);
     cx.cs = take(2 * (neig / 2 + 2));
     cx.pq = reinterpret_cast<int*>(take_bytes(sizeof(int) * (size_t)(neig / 2 + 2)));
-    cx.T = take((int64_t)neig * neig);
+    // the Jacobi method's warm-start product and saved bases exist only for the
+    // modes whose order is below the tridiagonal method's
+    int njac = 0;
+    for (int n = 0; n < p; ++n) {
+      const bool trd = cx.c[n] >= kTrdMinOrder && cx.ro[n] <= kTrdMaxRank;
+      if (!trd && cx.c[n] > njac) njac = cx.c[n];
+    }
+    cx.T = njac > 0 ? take((int64_t)njac * njac) : nullptr;
     {
       int rmx = 1;
       for (int n = 0; n < p; ++n) rmx = cx.ro[n] > rmx ? cx.ro[n] : rmx;
@@ -361,7 +369,10 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       for (int n = 0; n < p; ++n) cs *= (n == 0 ? (h.q[0] > h.nr0 ? h.q[0] : h.nr0) : h.q[n]);
       h.core = take(cs);
     }
-    for (int n = 0; n < p; ++n) cx.Vs[n] = take((int64_t)cx.c[n] * cx.c[n]);
+    for (int n = 0; n < p; ++n) {
+      const bool trd = cx.c[n] >= kTrdMinOrder && cx.ro[n] <= kTrdMaxRank;
+      cx.Vs[n] = trd ? nullptr : take((int64_t)cx.c[n] * cx.c[n]);
+    }
     for (int n = 1; n < p; ++n) {
       cx.phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
       cx.tau[n] = take(cx.k[n]);
@@ -469,7 +480,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       }
       G::sync();
       const long long c0 = clock64();
-      householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc);
+      householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
       qr_cyc += clock64() - c0;
       int tot = 1;
       for (int n = 0; n < p; ++n) {
@@ -501,10 +512,22 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     hn2 += sum_squares<G, S>(Hc, tot, sm.red);
   }
 
+  // Shared-memory staging for the Householder work on Phi_n: while Phi_n is
+  // factored (and again while Q_n is applied to the output), the arena from
+  // the eigensolver's matrices up to the factor blocks E holds nothing live,
+  // so Phi_n, when it lives in global memory, is worked on there.
+  auto staging = [&](int64_t nel) -> S* {
+    if (!__isShared(cx.A) || __isShared(cx.phi[1])) return nullptr;
+    const char* lim = __isShared(cx.E[0]) ? reinterpret_cast<const char*>(cx.E[0])
+                                          : reinterpret_cast<const char*>(arena + arena_bytes);
+    return (lim - reinterpret_cast<const char*>(cx.A)) >= (int64_t)(nel * sizeof(S)) ? cx.A : nullptr;
+  };
+
   // ---- non-temporal bases Phi_n = Q_n R_n, and the implicit HOSVD start ---
   for (int n = 1; n < p; ++n) {
     const int Dn = tv.D[n], kn = cx.k[n], cn = cx.c[n];
-    S* Phi = cx.phi[n];
+    S* stg = staging((int64_t)Dn * kn);
+    S* Phi = stg ? stg : cx.phi[n];
     for (int i = 0; i < nh; ++i) {
       const HitRec& h = hits[i];
       const S* F = reinterpret_cast<const S*>(tv.fac_pool[n]) + h.slot * tv.fac_stride[n];
@@ -516,12 +539,16 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     }
     G::sync();
     const long long c0 = clock64();
-    householder_qr<G, S>(Phi, Dn, kn, kn, cx.tau[n], sm.sc);
+    householder_qr<G, S>(Phi, Dn, kn, kn, cx.tau[n], sm.sc, sm.red, sm.wbuf);
     qr_cyc += clock64() - c0;
     S* R = cx.R[n];
     for (int idx = lane; idx < cn * kn; idx += nt) {
       const int a = idx / kn, b = idx % kn;
       R[idx] = (b >= a) ? Phi[a * kn + b] : S(0);
+    }
+    if (stg) {  // the reflectors are needed again for the output
+      for (int idx = lane; idx < Dn * kn; idx += nt) cx.phi[n][idx] = stg[idx];
+      G::sync();
     }
     for (int idx = lane; idx < cn * cn; idx += nt) A[idx] = 0;
     G::sync();
@@ -647,7 +674,8 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
         Y[t * ld0 + a] = (t < h.q[0]) ? Ci[t * ro[0] + a] : S(0);
       }
       G::sync();
-      householder_apply_q<G, S>(reinterpret_cast<S*>(h.slice), ell, h.q[0], h.nr0, reinterpret_cast<S*>(h.stau), Y, ro[0], ld0);
+      householder_apply_q<G, S>(reinterpret_cast<S*>(h.slice), ell, h.q[0], h.nr0, reinterpret_cast<S*>(h.stau), Y, ro[0],
+                                ld0, sm.wbuf);
     }
     if (ro[0] < rq[0]) {
       const int padc = rq[0] - ro[0];
@@ -657,15 +685,34 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   }
   for (int n = 1; n < p; ++n) {
     const int Dn = tv.D[n], cn = cx.c[n];
-    S* Y = un_dst[n];
-    const int64_t ld = ldn[n];
+    S* Yout = un_dst[n];
+    const int64_t ldo = ldn[n];
     const S* E = cx.E[n];
-    for (int idx = lane; idx < Dn * rq[n]; idx += nt) {
-      const int d = idx / rq[n], a = idx % rq[n];
-      Y[d * ld + a] = (a < ro[n] && d < cn) ? E[d * ro[n] + a] : S(0);
+    const int kn = cx.k[n];
+    // Q_n [E_n; 0], with Phi_n and the block staged in shared memory when possible
+    S* stg = staging((int64_t)Dn * kn + (int64_t)Dn * ro[n]);
+    const S* Ph = cx.phi[n];
+    S* Y = Yout;
+    int64_t ld = ldo;
+    if (stg) {
+      for (int idx = lane; idx < Dn * kn; idx += nt) stg[idx] = cx.phi[n][idx];
+      Ph = stg;
+      Y = stg + (int64_t)Dn * kn;
+      ld = ro[n];
+    }
+    for (int idx = lane; idx < Dn * ro[n]; idx += nt) {
+      const int d = idx / ro[n], a = idx % ro[n];
+      Y[d * ld + a] = d < cn ? E[d * ro[n] + a] : S(0);
     }
     G::sync();
-    householder_apply_q<G, S>(cx.phi[n], Dn, cn, cx.k[n], cx.tau[n], Y, ro[n], ld);
+    householder_apply_q<G, S>(Ph, Dn, cn, kn, cx.tau[n], Y, ro[n], ld, sm.wbuf);
+    if (stg || ro[n] < rq[n]) {
+      for (int idx = lane; idx < Dn * rq[n]; idx += nt) {
+        const int d = idx / rq[n], a = idx % rq[n];
+        Yout[d * ldo + a] = a < ro[n] ? Y[d * ld + a] : S(0);
+      }
+      G::sync();
+    }
   }
   if (lane == 0) {
     if (ranks_dst)
