@@ -183,3 +183,28 @@ def test_batch_equals_single_queries():
         assert np.array_equal(G, Gb[tuple(slice(0, x) for x in r)])
         assert all(np.array_equal(u, ub[:, :x]) for u, ub, x in zip(U, Ub, r))
         assert info[i].iters == inf["iters"]
+
+
+@pytest.mark.parametrize("dtype,bound", [("f64", 1e-9), ("f32", 2e-5)])
+def test_noise_free_low_rank_is_exact(dtype, bound):
+    """Noise-free data of Tucker rank (3, 3, 3) in a single regime, stored and
+    queried at ranks (6, 6, 6): every stage (leaf ALS, child merges, partial
+    hits, query stitch) is exact, so every query reconstructs its range to
+    rounding, as the oracle's own exactness pin states.  The Grams then have
+    exactly zero eigenvalues beyond rank 3, which the eigensolver has to treat
+    as one cluster (orders 20-30 here, so the tridiagonal method runs)."""
+    from oracle import metrics
+    dims, B, T = (30, 24), 4, 160
+    X = series(T, dims, (3, 3, 3), T, 0.0, 1234)
+    e = engine_tree(X, dims, (6, 6, 6), B, 5, 0.0, dtype)
+    Q = [(0, T), (5, 93), (17, 40), (3, 150), (60, 61), (128, 160)]
+    for ts, te in Q:
+        G, U, info = e.query(ts, te)
+        # materialized residual: the cancellation form of relative_error only
+        # resolves errors down to ~sqrt(eps)
+        Xs = np.asarray(X[ts:te], dtype=np.float64)
+        err = metrics.residual_norm_dense(Xs, np.float64(G), [np.float64(u) for u in U]) / np.linalg.norm(Xs)
+        assert err < bound, (ts, te, err, info)
+        for u in U:
+            u = np.float64(u)
+            assert np.abs(u.T @ u - np.eye(u.shape[1])).max() < (1e-10 if dtype == "f64" else 2e-5)
