@@ -243,6 +243,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fp32_plain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=3,
+                    help="timed launches of the 10,000-query batch at 200x150, rank 16 (0: skip)")
+    ap.add_argument("--appends", type=int, default=256,
+                    help="single-slice appends timed on the 4-way stream (0: skip)")
+    ap.add_argument("--appends-only", action="store_true",
+                    help="run only the append-latency section and print it")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the serving run (appends at 1 kHz; 15.36 s covers T 1024 -> 16384)")
     args = ap.parse_args()
@@ -254,6 +260,11 @@ def main():
 
     import torch
     import paper_2501_06647_gb300 as tk
+
+    if args.appends_only:
+        torch.cuda.set_device(0)
+        print(json.dumps({"appends": append_section(tk, torch, torch.device("cuda", 0), 0, args.appends)}))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -391,6 +402,11 @@ def main():
     torch.cuda.empty_cache()
 
     # ---- serving: interleaved appends and Poisson queries through the server -----
+    batched_sample = None
+    if args.batched_steps > 0:
+        line["batched_r16"], batched_sample = batched_section(tk, torch, dev, local, args.batched_steps)
+    if args.appends > 0:
+        line["appends"] = append_section(tk, torch, dev, local, args.appends)
     if args.serve_seconds > 0:
         line["serving"] = serving_section(tk, torch, dev, local, args.serve_seconds)
 
@@ -398,6 +414,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cpu_section(line, w, X, Q, offsets, tree, out_chk, info, n_q)
+            if batched_sample is not None:
+                batched_accuracy(line["batched_r16"], batched_sample)
         except Exception as exc:  # report, do not lose the GPU measurement
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                     "sample": None, "error": f"{type(exc).__name__}: {exc}"}
@@ -407,6 +425,145 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def batched_section(tk, torch, dev, local, steps):
+    """The batched form at larger shapes: 200x150 slices, T = 8192, ranks 16,
+    leaf 16, FP32; one launch sequence answers 10,000 concurrent queries of
+    log-uniform length 16..8192.  L2 flushed between timed launches.  Returns
+    the report and, for the accuracy check of the CPU leg, the outputs of a
+    sample of short queries."""
+    w = synth.WORKLOADS["batched_r16"]
+    X = synth.piecewise_tucker_regimes(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
+    stream = torch.cuda.Stream(device=dev)
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local,
+                   stream=stream)
+    Xd = torch.from_numpy(X).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree.build(Xd)
+    tree.sync()
+    build_s = time.perf_counter() - t0
+    del Xd
+    offsets = tree.layout(Q)
+    ranges_d = torch.from_numpy(Q.copy()).to(dev)
+    offsets_d = torch.from_numpy(offsets).to(dev)
+    out_d = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        tree.query_batch(ranges_d, offsets_d, out_d)
+    tree.sync()
+    ms = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.query_batch(ranges_d, offsets_d, out_d)
+            b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    tree.sync()
+    # sample for the accuracy check: queries of length <= 256 (Tucker-ALS from scratch stays cheap)
+    idx = [i for i in range(len(Q)) if Q[i][1] - Q[i][0] <= 256][:8]
+    sample = []
+    for i in idx:
+        ts, te = int(Q[i][0]), int(Q[i][1])
+        flat = out_d[int(offsets[i]):int(offsets[i + 1])].cpu().numpy()
+        G, U = tree.unpack(flat, te - ts)
+        sample.append((X[ts:te], G, U, list(w["ranks"])))
+    out_bytes = int(offsets[-1]) * 4
+    tree.close()
+    del out_d, flush
+    torch.cuda.empty_cache()
+    mean_ms = float(np.mean(ms))
+    return {
+        "workload": f"{w['dims'][0]}x{w['dims'][1]}xT={w['T']} piecewise Tucker rank-{tuple(w['ranks'])}, regime "
+                    f"{w['regime']}, sigma {w['sigma']}, leaf {w['B']}, {w['n_queries']} concurrent log-uniform "
+                    f"queries L in [{w['lo']},{w['hi']}], FP32, max_iter 20, tol 0.01",
+        "queries_per_s": len(Q) / (mean_ms / 1e3), "batch_ms": mean_ms, "steps": steps,
+        "tree_build_s": build_s, "output_bytes_per_batch": out_bytes,
+        "l2": "flushed between timed launches",
+    }, sample
+
+
+def batched_accuracy(rep_, sample):
+    """Paper's metric (Section 8.1) on the sampled queries: ||X - Y|| / ||X - Y_ALS|| - 1,
+    Y_ALS being Tucker-ALS from scratch on the raw subtensor (FP64 oracle)."""
+    from oracle import metrics
+    rel, errs = [], []
+    for Xs, G, U, ranks in sample:
+        Xs = np.asarray(Xs, dtype=np.float64)
+        G = np.float64(G)
+        U = [np.float64(u) for u in U]
+        Ga, Ua, _, _ = metrics.from_scratch(Xs, ranks)
+        rel.append(metrics.paper_relative_error(Xs, G, U, Ga, Ua))
+        errs.append(metrics.relative_error(Xs, G, U))
+    rep_["accuracy"] = {"queries": len(rel), "mean_paper_relative_error": float(np.mean(rel)) if rel else None,
+                        "max_paper_relative_error": float(np.max(rel)) if rel else None,
+                        "mean_rel_err": float(np.mean(errs)) if errs else None,
+                        "metric": "||X - Y|| / ||X - Y_ALS|| - 1 against FP64 Tucker-ALS from scratch, "
+                                  "queries of length <= 256"}
+
+
+def append_section(tk, torch, dev, local, n_app):
+    """Stream-update latency (Algorithms 3-4) on the 4-way 64x64x32 stream
+    (ranks 8, leaf 16, FP32): the tree is built to T0 = 1024, then n_app
+    single slices already in device memory are appended one at a time, each
+    timed with CUDA events on the tree's stream.  Every 16th append completes
+    a leaf block: Tucker-ALS of the block plus the Stitch of every newly
+    complete ancestor.  The others only store the slice (the open block is
+    decomposed when a query reaches into it); the cost of that is timed too,
+    as one query over the last 40 slices right after each append."""
+    w = synth.WORKLOADS["serving_4way"]
+    T0 = w["T0"]
+    X = synth.piecewise_tucker_regimes(T0 + n_app, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    stream = torch.cuda.Stream(device=dev)
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local,
+                   stream=stream)
+    Xd = torch.from_numpy(X).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree.build(Xd[:T0])
+    tree.sync()
+    build_s = time.perf_counter() - t0
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    app, done, tail = [], [], []
+    for k in range(n_app):
+        T = tree.T
+        a = ev()
+        tree.append(Xd[T])
+        b = ev()
+        r = torch.tensor([[max(0, T + 1 - 40), T + 1]], dtype=torch.int64, device=dev)
+        o = torch.from_numpy(tree.layout(r.cpu().numpy())).to(dev)
+        out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
+        c = ev()
+        tree.query_batch(r, o, out)
+        d = ev()
+        tree.sync()
+        (done if (T + 1) % w["B"] == 0 else app).append(a.elapsed_time(b))
+        if (T + 1) % w["B"] != 0:
+            tail.append(c.elapsed_time(d))
+    tree.close()
+    q = lambda v, f: sorted(v)[min(len(v) - 1, int(f * len(v)))] if v else None
+    return {
+        "workload": f"4-way {w['dims'][0]}x{w['dims'][1]}x{w['dims'][2]} slices, ranks {w['ranks']}, leaf {w['B']}, "
+                    f"FP32, tol 0.01; tree built to T={T0} ({build_s * 1e3:.1f} ms), then {n_app} appends",
+        "append_ms": {"mean": float(np.mean(app)) if app else None, "p99": q(app, 0.99),
+                      "what": "slice stored in the open block"},
+        "block_complete_ms": {"mean": float(np.mean(done)) if done else None, "max": max(done) if done else None,
+                              "count": len(done),
+                              "what": "leaf Tucker-ALS + Stitch of the newly complete ancestors"},
+        "open_block_query_ms": {"mean": float(np.mean(tail)) if tail else None, "p99": q(tail, 0.99),
+                                "what": "query over the last 40 slices, decomposing the open block first"},
+    }
 
 
 def serving_section(tk, torch, dev, local, seconds):

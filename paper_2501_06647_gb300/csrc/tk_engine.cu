@@ -331,6 +331,7 @@ TkLeafLayout leaf_layout(const tk_tree* t, int nsm, int64_t* per_cluster) {
   ly.half = neig / 2 + 2;
   ly.eig_in_smem = neig <= nsm;
   if (!ly.eig_in_smem) {
+    ly.nsm = 0;  // the eigensolver works in the CTA's global region: no shared arrays
     ly.A = take(neig * neig);
     ly.V = take(neig * neig);
     ly.w = take(neig + 2);

@@ -123,6 +123,12 @@ WORKLOADS = {
     "fp32_plain": dict(T=4096, dims=(100, 100), ranks=(10, 10, 10), regime=512, sigma=0.05, B=16,
                        n_queries=1000, kind="loguniform", lo=16, hi=4096, seed=1002, qseed=2002,
                        dtype="f32"),
+    # Batched form at larger shapes: 200x150 slices, T = 8192, ranks 16, 10,000
+    # concurrent queries of log-uniform length (generated regime by regime in
+    # float32, like the serving stream).
+    "batched_r16": dict(T=8192, dims=(200, 150), ranks=(16, 16, 16), regime=512, sigma=0.05, B=16,
+                        n_queries=10000, kind="loguniform", lo=16, hi=8192, seed=1003, qseed=2003,
+                        dtype="f32"),
     # 4-way stream grown by single-slice appends at append_hz while Poisson
     # range queries of log-uniform length (16..T) arrive at query_hz.
     "serving_4way": dict(T0=1024, T_end=16384, dims=(64, 64, 32), ranks=(8, 8, 8, 8), regime=512, sigma=0.05,

@@ -208,3 +208,25 @@ def test_noise_free_low_rank_is_exact(dtype, bound):
         for u in U:
             u = np.float64(u)
             assert np.abs(u.T @ u - np.eye(u.shape[1])).max() < (1e-10 if dtype == "f64" else 2e-5)
+
+
+def test_fp32_rank16_wide_slices_matches_fp64_oracle():
+    """The batched workload's shapes (200 x 150 slices, ranks 16, leaf 16) on
+    a shorter series: leaf Grams of order 200 (eigensolver arrays in global
+    memory), query eigenproblems of order up to ~100.  Hit sets bit for bit;
+    the FP32 model within 1e-3 ||X|| of the FP64 oracle's, as for the plain
+    workload."""
+    dims, ranks = (200, 150), (16, 16, 16)
+    T, B = 256, 16
+    X = series(T, dims, ranks, 128, 0.05, 1003)
+    o = oracle_tree(X, dims, ranks, B, 3, 0.0)
+    e = engine_tree(X, dims, ranks, B, 3, 0.0, "f32")
+    Q = synth.query_ranges(T, 8, 2003, "loguniform", 16, T)
+    for ts, te in Q:
+        assert [tuple(h[:6]) for h in e.hit_set(int(ts), int(te))] == o.hit_records(int(ts), int(te))
+        ro = o.query(int(ts), int(te))
+        Ge, Ue, info = e.query(int(ts), int(te))
+        assert info["ranks"] == ro["ranks"]
+        rel, dist, ang, ee, eo = compare(X, int(ts), int(te), Ge, Ue, ro["G"], ro["U"])
+        assert dist < 1e-3, (ts, te, dist)
+        assert abs(ee - eo) < 1e-3 * max(eo, 0.1), (ts, te, ee, eo)
