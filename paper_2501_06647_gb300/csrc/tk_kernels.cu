@@ -1,7 +1,8 @@
 // Kernels of the range-query Tucker engine.
 //
 //  k_hitset  Algorithm 1 (Recall) over the implicit dyadic stream segment tree.
-//  k_stitch  one WARP per job, jobs taken from a dynamic queue; a job is a
+//  k_plan    longest-first processing order of a query batch.
+//  k_stitch  one CTA per job, jobs taken from a dynamic queue; a job is a
 //            range query (Section 6.1: Recall, Eq. (partial-tucker),
 //            Algorithm 2) or the re-decomposition of a newly complete node
 //            from its two children (Algorithm 3, Stitch).
@@ -22,10 +23,10 @@
 // Phi_n and the final factor assembly.  This is an exact rewrite: the result
 // is Algorithm 2's iterate, up to rounding order.
 //
-// A job's problems are tiny (eig orders ~ sum_i r_i, tensors of r^p
-// elements), so one warp owns a job and synchronizes with __syncwarp only;
-// thousands of queries of a batch run concurrently, one per resident warp.
-// Each eigenproblem of an ALS iteration is warm-started from the same mode's
+// A job's problems are small (eig orders ~ sum_i r_i, tensors of r^p
+// elements): one CTA owns a job, its hottest buffers in a shared-memory
+// arena.  Eigenproblems of order >= kTrdMinOrder use the tridiagonal top-r
+// method; smaller ones use Jacobi, warm-started from the same mode's
 // eigenvectors of the previous iteration (or of the initialization).
 #include <cstdio>
 
