@@ -56,6 +56,32 @@ struct BlockGroup {
   }
 };
 
+// Half of a 512-thread CTA (256 threads) with its own named barrier (ids 1
+// and 2; 0 is __syncthreads), so that the two halves run independent jobs.
+struct HalfGroup {
+  static __device__ __forceinline__ int half() { return threadIdx.x >> 8; }
+  static __device__ __forceinline__ int rank() { return threadIdx.x & 255; }
+  static __device__ __forceinline__ int size() { return 256; }
+  static __device__ __forceinline__ int nwarps() { return 8; }
+  static __device__ __forceinline__ void sync() { asm volatile("bar.sync %0, 256;" ::"r"(1 + half()) : "memory"); }
+  template <class S> static __device__ S sum(S v, S* red) {
+    v = warp_sum(v);
+    const int lane = rank() & 31, warp = rank() >> 5;
+    sync();
+    if (lane == 0) red[warp] = v;
+    sync();
+    if (warp == 0) {
+      S x = lane < 8 ? red[lane] : S(0);
+      x = warp_sum(x);
+      if (lane == 0) red[32] = x;
+    }
+    sync();
+    const S r = red[32];
+    sync();
+    return r;
+  }
+};
+
 template <class G, class S> __device__ S sum_squares(const S* x, int64_t n, S* red) {
   S a = 0;
   for (int64_t i = G::rank(); i < n; i += G::size()) a += x[i] * x[i];
@@ -198,14 +224,14 @@ __device__ void gemm(int M, int N, int K, const S* A, int ars, int acs, const S*
 // Applies the reflector H = I - tau v v^T, v = (1, A[r0+1..m-1][j]) (column
 // j of A below row r0), to columns [0, nc) of B (rows r0..m-1, leading
 // dimension ldb): w_c = tau (B[r0][c] + sum_{i>r0} v_i B[i][c]), then
-// B[r0][c] -= w_c and B[i][c] -= w_c v_i.  Every thread of the CTA takes a
+// B[r0][c] -= w_c and B[i][c] -= w_c v_i.  Every thread of the group takes a
 // share of the rows and accumulates the dot products of up to 16 columns at
 // once; one reduction then serves all of them.  For tall matrices (m much
 // larger than the CTA), where one warp per column would walk the rows alone.
 // wbuf: >= 16 * (nwarps + 1) elements of shared scratch.
-template <class S>
+template <class G, class S>
 __device__ void reflect_cols(const S* A, int lda, int j, int r0, int m, S tau, S* B, int64_t ldb, int nc, S* wbuf) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  const int tid = G::rank(), nt = G::size(), lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   S* wfin = wbuf + 16 * nw;
   for (int c0 = 0; c0 < nc; c0 += 16) {
     const int cw = nc - c0 < 16 ? nc - c0 : 16;
@@ -223,7 +249,7 @@ __device__ void reflect_cols(const S* A, int lda, int j, int r0, int m, S tau, S
     for (int c = 0; c < 16; ++c) acc[c] = warp_sum(acc[c]);
     if (lane == 0)
       for (int c = 0; c < cw; ++c) wbuf[warp * 16 + c] = acc[c];
-    __syncthreads();
+    G::sync();
     if (tid < cw) {
       S w = B[r0 * ldb + c0 + tid];
       for (int q = 0; q < nw; ++q) w += wbuf[q * 16 + tid];
@@ -231,13 +257,13 @@ __device__ void reflect_cols(const S* A, int lda, int j, int r0, int m, S tau, S
       wfin[tid] = w;
       B[r0 * ldb + c0 + tid] -= w;
     }
-    __syncthreads();
+    G::sync();
     for (int i = r0 + 1 + tid; i < m; i += nt) {
       const S vi = A[(int64_t)i * lda + j];
       S* bp = B + i * ldb + c0;
       for (int c = 0; c < cw; ++c) bp[c] -= wfin[c] * vi;
     }
-    __syncthreads();
+    G::sync();
   }
 }
 
@@ -279,7 +305,7 @@ __device__ void householder_qr(S* A, int m, int n, int lda, S* tau, S* sc, S* re
       if (t != S(0)) {
         for (int i = j + 1 + G::rank(); i < m; i += G::size()) A[(int64_t)i * lda + j] *= scale;
         G::sync();
-        reflect_cols<S>(A, lda, j, j, m, t, A + j + 1, lda, n - j - 1, wbuf);
+        reflect_cols<G, S>(A, lda, j, j, m, t, A + j + 1, lda, n - j - 1, wbuf);
       }
       if (G::rank() == 0) A[(int64_t)j * lda + j] = beta;
       G::sync();
@@ -339,7 +365,7 @@ __device__ void householder_apply_q(const S* A, int m, int kmax, int lda, const 
   const int lane = G::rank() & 31, warp = G::rank() >> 5, nw = G::nwarps();
   if (wbuf && G::nwarps() > 1 && m >= 2 * G::size()) {
     for (int j = kmax - 1; j >= 0; --j)
-      if (tau[j] != S(0)) reflect_cols<S>(A, lda, j, j, m, tau[j], Y, ldy, ncols, wbuf);
+      if (tau[j] != S(0)) reflect_cols<G, S>(A, lda, j, j, m, tau[j], Y, ldy, ncols, wbuf);
     return;
   }
   for (int j = kmax - 1; j >= 0; --j) {

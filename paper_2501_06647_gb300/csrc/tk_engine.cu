@@ -60,9 +60,6 @@ struct tk_tree {
   int sm_count = 0;
   // staging for host io and batch metadata
   DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
-  // heavy queries of a batch run on a second, high-priority stream
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_plan = nullptr, ev_heavy = nullptr;
   int64_t launches = 0;
 };
 
@@ -398,16 +395,15 @@ int ensure_ws_leaf(tk_tree* t, int want_clusters, TkLeafLayout* ly) {
   return TK_OK;
 }
 
-// Heavy queries (hit sets of at least heavy_hits() nodes, eigenproblem orders
-// >= ~45) run in CTAs of heavy_warps() warps with a shared arena of
-// heavy_arena() bytes (one CTA per SM), concurrently with the light ones.
+// Heavy queries: hit sets of at least heavy_hits() nodes (eigenproblem
+// orders >= ~45); k_batch runs them with a whole CTA.
 int heavy_hits(const tk_tree* t) {
   int r = 1;
   for (int n = 0; n < t->p; ++n) r = std::max(r, t->cfg.ranks[n]);
   return std::max(3, (45 + r - 1) / r);
 }
-int heavy_warps(const tk_tree* t) { (void)t; return 16; }
-size_t heavy_arena(const tk_tree* t) { (void)t; return 200 * 1024; }
+// Shared arena of one half of a k_batch CTA; a heavy query gets both halves.
+size_t batch_half_arena(const tk_tree* t) { (void)t; return 100 * 1024; }
 
 TkWorkspace ws_view(const tk_tree* t, bool leaf) {
   TkWorkspace w{};
@@ -490,7 +486,7 @@ int64_t out_elems(const tk_tree* t, int64_t L, const int* rq) {
   return c;
 }
 
-// One batch launch sequence (plan, heavy part on the side stream, light part)
+// One batch launch sequence (plan, then the batch kernel; a single query runs alone)
 // with all pointers on the device.  Asynchronous on the tree's stream.
 int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_offsets, const int* rq, void* d_out,
                  tk_query_info* d_info, const int64_t* d_tq = nullptr) {
@@ -509,20 +505,13 @@ int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_of
   qb.tq = d_tq;
   for (int k = 0; k < TK_MAXP; ++k) qb.rq[k] = rq[k];
   if (n > 1) {
-    // longest-first order; the heavy head of it runs on the side stream in
-    // big CTAs while the rest runs here, and this stream waits for both
-    if (!t->side) {
-      int lo = 0, hi = 0;
-      cudaDeviceGetStreamPriorityRange(&lo, &hi);
-      if (cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
-          cudaEventCreateWithFlags(&t->ev_plan, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&t->ev_heavy, cudaEventDisableTiming) != cudaSuccess)
-        return TK_ERR_CUDA;
-    }
-    const int hgrid = std::min(n, t->sm_count);
+    // Longest-first order (k_plan), then one k_batch launch: a CTA per SM
+    // runs the heavy head of the order with all its threads and then the
+    // light rest in two halves (see k_batch).
+    const int bgrid = std::min(n, t->sm_count);
     const int64_t per = stitch_ws_bound(t, max_hits(t, t->nbcap));
     rc = dalloc(t->plan, sizeof(int) * ((size_t)n + 4));
-    if (rc == TK_OK) rc = ensure_ws_stitch(t, grid + hgrid);
+    if (rc == TK_OK) rc = ensure_ws_stitch(t, 2 * bgrid);
     if (rc) return rc;
     int* split = (int*)t->plan.ptr;
     int* order = split + 4;
@@ -531,23 +520,11 @@ int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_of
     if (rc) return rc;
     qb.order = order;
     qb.split = split;
-    TkWorkspace wl = ws_view(t, false), wh = ws_view(t, false);
-    wh.base = (char*)t->ws_stitch.ptr + (size_t)grid * per * t->es;
-    wh.warps = heavy_warps(t);
-    wh.smem_arena = heavy_arena(t);
-    wh.counter = (unsigned*)((char*)t->status.ptr + 20);
-    rc = cuda_ok(cudaEventRecord(t->ev_plan, t->stream));
-    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->side, t->ev_plan, 0));
-    if (rc) return rc;
-    qb.part = 1;
-    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wh, hgrid, t->side);
+    TkWorkspace wb = ws_view(t, false);
+    wb.per_cta = per;
+    wb.smem_arena = batch_half_arena(t);
+    rc = tk_launch_batch(t->cfg.dtype, make_view(t), qb, wb, bgrid, t->stream);
     t->launches += 1;
-    if (rc == TK_OK) rc = cuda_ok(cudaEventRecord(t->ev_heavy, t->side));
-    if (rc) return rc;
-    qb.part = 2;
-    rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, wl, grid, t->stream);
-    t->launches += 1;
-    if (rc == TK_OK) rc = cuda_ok(cudaStreamWaitEvent(t->stream, t->ev_heavy, 0));
   } else {
     rc = tk_launch_query(t->cfg.dtype, make_view(t), qb, ws_view(t, false), grid, t->stream);
     t->launches += 1;
@@ -650,9 +627,6 @@ void tk_tree_destroy(tk_tree* t) {
                     &t->plan};
   for (DevBuf* b : bufs) dfree(*b);
   for (int n = 0; n < TK_MAXP; ++n) dfree(t->fac_pool[n]);
-  if (t->side) cudaStreamDestroy(t->side);
-  if (t->ev_plan) cudaEventDestroy(t->ev_plan);
-  if (t->ev_heavy) cudaEventDestroy(t->ev_heavy);
   if (t->own_stream && t->stream) cudaStreamDestroy(t->stream);
   delete t;
 }

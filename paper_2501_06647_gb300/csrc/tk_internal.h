@@ -105,6 +105,12 @@ int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int 
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
 int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);
+// k_batch: one 512-thread CTA per SM for a planned batch (order, split); the
+// workspace holds 2 chunks of ws.per_cta elements per CTA, ws.smem_arena is
+// the arena of one half.
+int tk_launch_batch(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, const TkWorkspace& ws, int grid,
+                    cudaStream_t stream);
+size_t tk_batch_smem_bytes(int dtype, size_t half_arena);
 // order[0..n) longest first; *split = how many queries have >= heavy_hits hits.
 int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, const int64_t* tq, int heavy_hits, int* split,
                    int* order, cudaStream_t stream);

@@ -230,7 +230,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
                            const int* rq, S* ws, int64_t ws_cap, size_t arena_bytes, S* core_dst, S* u0_dst,
                            int64_t ld0,
                            S* const* un_dst, const int64_t* ldn, int* ranks_dst, tk_query_info* info,
-                           int* status, unsigned char* wsm_raw) {
+                           int* status, unsigned char* wsm_raw, unsigned char* arena) {
   WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(wsm_raw);
   StitchCtx<S>& cx = sm.ctx;
   const long long t_start = clock64();
@@ -239,7 +239,6 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   const int p = tv.p;
   const int lane = G::rank();
   const int nt = G::size();
-  unsigned char* arena = wsm_raw + align16(sizeof(WarpSm<S>));
 
   if (lane == 0) {
     cx.err = 0;
@@ -733,21 +732,49 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   G::sync();
 }
 
-// Stitch kernel: each group (a warp or the whole CTA, per G) repeatedly
-// takes the next job index from the launch's queue counter (zeroed by the
-// host before the launch) and runs it.
+// One range query of a batch (index q) by group G: validation against the
+// query's epoch, output pointers into the packed output, then the stitch.
+template <class G, class S>
+__device__ void query_job(const TkTreeView& tv, const TkQueryBatch& qb, int q, S* ws, int64_t ws_cap,
+                          size_t arena_bytes, int* status, unsigned char* wsm, unsigned char* arena) {
+  const int64_t ts = qb.ranges[2 * q], te = qb.ranges[2 * q + 1];
+  S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[q];
+  tk_query_info* info = qb.info ? qb.info + q : nullptr;
+  const TkEpoch ep = (qb.tq && qb.tq[q] <= tv.T) ? epoch_at(tv, qb.tq[q]) : epoch_now(tv);
+  if (!(ts >= 0 && ts < te && te <= ep.T)) {
+    if (G::rank() == 0) {
+      set_err(status, TK_DEV_ERR_RANGE);
+      if (info) info->iters = -TK_DEV_ERR_RANGE;
+    }
+    G::sync();
+    return;
+  }
+  int64_t ctot = 1;
+  for (int n = 0; n < tv.p; ++n) ctot *= qb.rq[n];
+  S* u0 = out + ctot;
+  S* un[TK_MAXP];
+  int64_t ldn[TK_MAXP];
+  S* cur = u0 + (te - ts) * qb.rq[0];
+  for (int n = 1; n < tv.p; ++n) {
+    un[n] = cur;
+    ldn[n] = qb.rq[n];
+    cur += (int64_t)tv.D[n] * qb.rq[n];
+  }
+  stitch_job<G, S>(tv, ep, TK_JOB_QUERY, ts, te, 0, 0, qb.rq, ws, ws_cap, arena_bytes, out, u0, qb.rq[0], un, ldn,
+                   nullptr, info, status, wsm, arena);
+}
+
+// Stitch kernel: each CTA repeatedly takes the next job index from the
+// launch's queue counter (zeroed by the host before the launch) and runs it.
 template <class S, class G>
 __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, int level, int64_t k0,
                                                       int njobs, TkQueryBatch qb, TkWorkspace wsd) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int grp = G::size() == 32 ? (int)(threadIdx.x >> 5) : 0;
-  const int ngrp = G::size() == 32 ? (int)(blockDim.x >> 5) : 1;
   const int tid = G::rank();
-  const size_t gbytes = group_smem_bytes<S>(wsd.smem_arena);
-  unsigned char* gsm = smem_raw + grp * gbytes;
+  unsigned char* gsm = smem_raw;
+  unsigned char* arena = smem_raw + align16(sizeof(WarpSm<S>));
   WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(gsm);
-  const int64_t gid = (int64_t)blockIdx.x * ngrp + grp;
-  S* ws = reinterpret_cast<S*>(wsd.base) + gid * wsd.per_cta;
+  S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
   int job_lo = 0, job_hi = njobs;
   if (qb.part == 1) job_hi = *qb.split;
   if (qb.part == 2) job_lo = *qb.split;
@@ -758,32 +785,8 @@ __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, i
     G::sync();
     if (job >= job_hi) break;
     if (mode == TK_JOB_QUERY) {
-      const int q = qb.order ? qb.order[job] : job;
-      const int64_t ts = qb.ranges[2 * q], te = qb.ranges[2 * q + 1];
-      S* out = reinterpret_cast<S*>(qb.out) + qb.offsets[q];
-      tk_query_info* info = qb.info ? qb.info + q : nullptr;
-      const TkEpoch ep = (qb.tq && qb.tq[q] <= tv.T) ? epoch_at(tv, qb.tq[q]) : epoch_now(tv);
-      if (!(ts >= 0 && ts < te && te <= ep.T)) {
-        if (tid == 0) {
-          set_err(wsd.status, TK_DEV_ERR_RANGE);
-          if (info) info->iters = -TK_DEV_ERR_RANGE;
-        }
-        G::sync();
-        continue;
-      }
-      int64_t ctot = 1;
-      for (int n = 0; n < tv.p; ++n) ctot *= qb.rq[n];
-      S* u0 = out + ctot;
-      S* un[TK_MAXP];
-      int64_t ldn[TK_MAXP];
-      S* cur = u0 + (te - ts) * qb.rq[0];
-      for (int n = 1; n < tv.p; ++n) {
-        un[n] = cur;
-        ldn[n] = qb.rq[n];
-        cur += (int64_t)tv.D[n] * qb.rq[n];
-      }
-      stitch_job<G, S>(tv, ep, mode, ts, te, 0, 0, qb.rq, ws, wsd.per_cta, wsd.smem_arena, out, u0, qb.rq[0], un,
-                       ldn, nullptr, info, wsd.status, gsm);
+      query_job<G, S>(tv, qb, qb.order ? qb.order[job] : job, ws, wsd.per_cta, wsd.smem_arena, wsd.status, gsm,
+                      arena);
     } else {
       const int64_t k = k0 + job;
       const int64_t slot = tv.level_base[level] + k;
@@ -796,9 +799,60 @@ __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, i
         ldn[n] = tv.r[n];
       }
       stitch_job<G, S>(tv, epoch_now(tv), mode, 0, 0, level, k, tv.r, ws, wsd.per_cta, wsd.smem_arena, core, u0,
-                       tv.r[0], un,
-                       ldn, tv.node_ranks + slot * TK_MAXP, nullptr, wsd.status, gsm);
+                       tv.r[0], un, ldn, tv.node_ranks + slot * TK_MAXP, nullptr, wsd.status, gsm, arena);
     }
+  }
+}
+
+// Batch kernel: one 512-thread CTA per SM, jobs taken longest first from one
+// queue (the planned order).  While the queue still holds heavy queries (the
+// first *qb.split of the order), a CTA runs each with all 16 warps and a
+// shared arena of 2 * smem_arena bytes.  The first light job a CTA draws
+// switches it to two independent 256-thread halves (named barriers), each
+// with its own header, arena of smem_arena bytes and workspace chunk, each
+// drawing light jobs until the queue is empty.  Heavy and light queries thus
+// share every SM in the order planned, whatever order the hardware starts
+// CTAs in.  Shared memory: [header 0][header 1][arena 2 * smem_arena].
+template <class S>
+__global__ void __launch_bounds__(2 * TK_NT, 1) k_batch(TkTreeView tv, int njobs, TkQueryBatch qb, TkWorkspace wsd) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const size_t hdr = align16(sizeof(WarpSm<S>));
+  unsigned char* arena = smem_raw + 2 * hdr;
+  S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * 2 * wsd.per_cta;
+  WarpSm<S>& sm0 = *reinterpret_cast<WarpSm<S>*>(smem_raw);
+  const int split = qb.split ? *qb.split : 0;
+  int light = -1;
+  while (true) {
+    if (threadIdx.x == 0) sm0.job = (int)atomicAdd(wsd.counter, 1u);
+    __syncthreads();
+    const int job = sm0.job;
+    __syncthreads();
+    if (job >= njobs) return;
+    if (job >= split) {
+      light = job;
+      break;
+    }
+    query_job<BlockGroup, S>(tv, qb, qb.order ? qb.order[job] : job, ws, wsd.per_cta, 2 * wsd.smem_arena,
+                             wsd.status, smem_raw, arena);
+  }
+  // two halves from here on; half 0 starts with the light job already drawn
+  const int h = HalfGroup::half();
+  unsigned char* hsm = smem_raw + h * hdr;
+  WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(hsm);
+  unsigned char* harena = arena + h * wsd.smem_arena;
+  S* hws = ws + h * wsd.per_cta;
+  int job = h == 0 ? light : -1;
+  while (true) {
+    if (job < 0) {
+      if (HalfGroup::rank() == 0) sm.job = (int)atomicAdd(wsd.counter, 1u);
+      HalfGroup::sync();
+      job = sm.job;
+      HalfGroup::sync();
+    }
+    if (job >= njobs) break;
+    query_job<HalfGroup, S>(tv, qb, qb.order ? qb.order[job] : job, hws, wsd.per_cta, wsd.smem_arena, wsd.status,
+                            hsm, harena);
+    job = -1;
   }
 }
 
@@ -906,6 +960,26 @@ int tk_launch_query(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, con
                     cudaStream_t stream) {
   if (qb.n <= 0) return TK_OK;
   return launch_stitch(dtype, tv, TK_JOB_QUERY, 0, 0, qb.n, qb, ws, grid, stream);
+}
+
+size_t tk_batch_smem_bytes(int dtype, size_t half_arena) {
+  const size_t hdr = dtype == TK_F64 ? align16(sizeof(WarpSm<double>)) : align16(sizeof(WarpSm<float>));
+  return 2 * hdr + 2 * align16(half_arena);
+}
+
+int tk_launch_batch(int dtype, const TkTreeView& tv, const TkQueryBatch& qb, const TkWorkspace& ws, int grid,
+                    cudaStream_t stream) {
+  if (qb.n <= 0) return TK_OK;
+  const size_t smem = tk_batch_smem_bytes(dtype, ws.smem_arena);
+  if (cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), stream) != cudaSuccess) return TK_ERR_CUDA;
+  if (dtype == TK_F64) {
+    if (set_smem_attr((const void*)k_batch<double>, smem)) return TK_ERR_CUDA;
+    k_batch<double><<<grid, 2 * TK_NT, smem, stream>>>(tv, qb.n, qb, ws);
+  } else {
+    if (set_smem_attr((const void*)k_batch<float>, smem)) return TK_ERR_CUDA;
+    k_batch<float><<<grid, 2 * TK_NT, smem, stream>>>(tv, qb.n, qb, ws);
+  }
+  return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
 
 int tk_launch_plan(const TkTreeView& tv, int n, const int64_t* ranges, const int64_t* tq, int heavy_hits, int* split,
