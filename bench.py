@@ -33,10 +33,10 @@ METRIC = "range queries/sec + p50/p99 query latency at matched recon error vs pl
 UNIT = "queries/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes of one batch of the FP32 plain workload (heavy + light k_stitch
-# launches: 3.66 + 0.25 MB and 8.04 + 26.13 MB), from one ncu capture of the
-# current kernel; must be re-measured whenever the stitch kernel changes.
-STITCH_BATCH_DRAM_BYTES = 38.08e6
+# DRAM bytes of one batch of the FP32 plain workload (the k_batch launch),
+# from one ncu capture of the current kernel; None until measured, and to be
+# re-measured whenever the kernel changes.
+STITCH_BATCH_DRAM_BYTES = 40.38e6  # 8.76 MB read + 31.62 MB written
 
 
 def workload_desc(w):
@@ -381,9 +381,9 @@ def main():
     achieved = flops / avg_launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": STITCH_BATCH_DRAM_BYTES,
-                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of the two k_stitch launches of "
-                                "one batch, one ncu capture of this workload (bytes per batch)",
-                "kernel": "k_stitch<float>: one batch = its heavy and light launches, timed together",
+                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of the k_batch launch of one "
+                                "batch, one ncu capture of this workload (bytes per launch)",
+                "kernel": "k_batch<float> (one launch answers the whole batch)",
                 "flops_per_launch": flops,
                 "peak_note": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
 
