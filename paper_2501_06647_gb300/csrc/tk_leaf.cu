@@ -91,7 +91,7 @@ __device__ __forceinline__ int64_t prod64(const int* d, int a, int b) {
 // x_c x_c^T, where the columns are those of the mode-n matricization of a
 // C-order tensor seen as (outer, D, inner): x_c[a] = X[(o D + a) inner + i],
 // c = o inner + i.  One CTA: kKC columns at a time are staged in shared
-// memory (`tile`, kKC * round4(D) elements, 16-byte aligned) and every thread
+// memory (`tile`, kKC * (round4(D) + 4) elements, 16-byte aligned) and every thread
 // accumulates 4x4 blocks of the upper triangle, mirrored on output.  The
 // loads of the next kKC columns are issued into registers before the current
 // ones are used, so their latency overlaps the arithmetic.  Every entry sums
@@ -103,8 +103,10 @@ __device__ void gram_cols(const S* X, int D, int64_t inner, int64_t c0, int64_t 
   // float only: in double it would spill, and the double path is not hot)
   constexpr int PF = sizeof(S) == 4 ? 20 : 1;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int ld = (D + 3) & ~3;
-  const int nb4 = ld / 4;
+  // tile row length: D rounded to 4 for the float4 reads, plus 4 so that the
+  // column-per-lane stores of the inner > 1 path spread over 8 banks, not 1
+  const int ld = ((D + 3) & ~3) + 4;
+  const int nb4 = ((D + 3) & ~3) / 4;
   const int ntile = nb4 * (nb4 + 1) / 2;
   const int per = (kKC * ld + nt - 1) / nt;  // staged elements per thread
   const bool fits = sizeof(S) == 4 && per <= PF;
@@ -231,9 +233,16 @@ __device__ void ttm_staged(const S* X, int64_t outer, int dm, int inner, const S
     us[e] = al < a ? U[j * a + al] : S(0);
   }
   const int blk = dm * inner;
-  const int ob = kStage / blk;  // blocks per chunk
+  // staged stride of a block: one word more when a block is a single row
+  // (inner == 1), so that threads reading different rows at the same column
+  // hit different banks
+  const int bst = inner == 1 ? blk + 1 : blk;
+  const int ob = kStage / bst;  // blocks per chunk
   const int64_t nchunk = (outer + ob - 1) / ob;
   const int nch = a4 / 4;
+  // this thread's staging slots: element e = tid + u * nt of a chunk is
+  // (block e / blk, offset e % blk), walked with carries
+  const int db = nt / blk, doff = nt - db * blk;
   auto fetch = [&](int64_t ch, S* v) {
     const int64_t o0 = ch * ob;
     const int64_t cnt = ((outer - o0) < ob ? (outer - o0) : ob) * blk;
@@ -250,8 +259,19 @@ __device__ void ttm_staged(const S* X, int64_t outer, int dm, int inner, const S
     const int64_t o0 = ch * ob;
     const int nob = (int)((outer - o0) < ob ? (outer - o0) : ob);
     __syncthreads();  // the stage (and, first time, us) is free / ready
+    {
+      int b = tid / blk, off = tid - (tid / blk) * blk;
 #pragma unroll
-    for (int u = 0; u < PF; ++u) stage[tid + u * nt] = v[u];
+      for (int u = 0; u < PF; ++u) {
+        if (b < ob) stage[b * bst + off] = v[u];
+        off += doff;
+        b += db;
+        if (off >= blk) {
+          off -= blk;
+          ++b;
+        }
+      }
+    }
     __syncthreads();
     if (ch + 1 < nchunk) fetch(ch + 1, v);
     // items (ob, c4, i), i fastest
@@ -260,7 +280,7 @@ __device__ void ttm_staged(const S* X, int64_t outer, int dm, int inner, const S
       const int i = it % inner;
       const int t = it / inner;
       const int c4 = t % nch, b = t / nch;
-      const S* xs = stage + b * blk + i;
+      const S* xs = stage + b * bst + i;
       const S* ms = us + 4 * c4;
       S acc[4] = {S(0), S(0), S(0), S(0)};
       for (int j = 0; j < dm; ++j) {
@@ -329,7 +349,7 @@ __device__ void slab_rows(const S* X, const int* xd, const int* rl, int p, int n
   for (int m = p - 1; m >= 0; --m) {
     if (m == n) continue;
     const int64_t in = prod64(dims, m + 1, p);
-    if ((int64_t)dims[m] * in <= kStage)
+    if ((int64_t)dims[m] * in + 1 <= kStage)
       ttm_staged<S>(src, prod64(dims, 0, m), dims[m], (int)in, U[m], rl[m], dst, stage, us);
     else
       ttm<BlockGroup, S>(src, dims, p, m, U[m], 1, rl[m], rl[m], dst, false);
@@ -374,7 +394,7 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
   S* sV = reinterpret_cast<S*>(smem_raw + off);
   off += align16(sizeof(S) * (size_t)nsm * nsm);
   S* tile = reinterpret_cast<S*>(smem_raw + off);
-  off += align16(sizeof(S) * (size_t)kKC * ((ly.neig + 3) & ~3));
+  off += align16(sizeof(S) * (size_t)kKC * (((ly.neig + 3) & ~3) + 4));
   S* stage = reinterpret_cast<S*>(smem_raw + off);
   off += align16(sizeof(S) * (size_t)kStage);
   S* us = reinterpret_cast<S*>(smem_raw + off);
@@ -563,7 +583,7 @@ size_t tk_leaf_smem_bytes(int dtype, int nsm, int neig, int rmax) {
   size_t b = kHdr + align16(half_cap * sizeof(int));
   b += align16(es * (2 * half_cap + nsm + 2));
   b += 2 * align16(es * (size_t)nsm * nsm);
-  b += align16(es * (size_t)kKC * ((neig + 3) & ~3));
+  b += align16(es * (size_t)kKC * (((neig + 3) & ~3) + 4));
   b += align16(es * (size_t)kStage);
   b += es * (size_t)neig * ((rmax + 3) & ~3);
   return b;
