@@ -251,6 +251,8 @@ def main():
                     help="timed launches of the 10,000-query batch at 200x150, rank 16 (0: skip)")
     ap.add_argument("--appends", type=int, default=256,
                     help="single-slice appends timed on the 4-way stream (0: skip)")
+    ap.add_argument("--theta-sweep", action="store_true",
+                    help="run only the pruning-threshold sweep (theta 0.5, 0.7, 0.9) and print it")
     ap.add_argument("--appends-only", action="store_true",
                     help="run only the append-latency section and print it")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
@@ -265,6 +267,10 @@ def main():
     import torch
     import paper_2501_06647_gb300 as tk
 
+    if args.theta_sweep:
+        torch.cuda.set_device(0)
+        print(json.dumps({"theta_sweep": theta_sweep(tk, torch, torch.device("cuda", 0), 0)}))
+        return 0
     if args.appends_only:
         torch.cuda.set_device(0)
         print(json.dumps({"appends": append_section(tk, torch, torch.device("cuda", 0), 0, args.appends)}))
@@ -512,6 +518,56 @@ def batched_accuracy(rep_, sample):
                         "mean_rel_err": float(np.mean(errs)) if errs else None,
                         "metric": "||X - Y|| / ||X - Y_ALS|| - 1 against FP64 Tucker-ALS from scratch, "
                                   "queries of length <= 256"}
+
+
+def theta_sweep(tk, torch, dev, local, thetas=((1, 2), (7, 10), (9, 10))):
+    """Pruning threshold theta (Section 5.1, Algorithm 1) on the FP32 plain
+    workload: per theta, the batch throughput, the mean hit-set size and
+    iteration count, and the mean relative error ||X - Y|| / ||X|| of 100
+    sampled queries (the reconstruction materialized on the GPU in FP64)."""
+    w = synth.WORKLOADS["fp32_plain"]
+    X = synth.piecewise_tucker(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
+    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+    X64 = torch.from_numpy(X).to(dev)
+    rows = []
+    for num, den in thetas:
+        stream = torch.cuda.Stream(device=dev)
+        tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], theta=(num, den), max_iter=20, tol=0.01,
+                       dtype="f32", device=local, stream=stream)
+        tree.build(Xd)
+        tree.sync()
+        offsets = tree.layout(Q)
+        rd = torch.from_numpy(Q.copy()).to(dev)
+        od = torch.from_numpy(offsets).to(dev)
+        out = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        ms = []
+        for k in range(6):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tree.query_batch(rd, od, out)
+                b.record(stream)
+            b.synchronize()
+            if k >= 2:
+                ms.append(a.elapsed_time(b))
+        _, _, info = tree.query_batch_host(Q, offsets, None, with_info=True)
+        errs = []
+        for i in range(0, len(Q), len(Q) // 100):
+            ts, te = int(Q[i][0]), int(Q[i][1])
+            G, U = tree.unpack(out[int(offsets[i]):int(offsets[i + 1])], te - ts)
+            Y = torch.einsum("abc,ia,jb,kc->ijk", G.double(), U[0].double(), U[1].double(), U[2].double())
+            Xs = X64[ts:te]
+            errs.append(float(torch.linalg.norm(Xs - Y) / torch.linalg.norm(Xs)))
+        rows.append({"theta": num / den, "queries_per_s": len(Q) / (np.mean(ms) / 1e3), "batch_ms": float(np.mean(ms)),
+                     "mean_hits": float(np.mean([f.n_hits for f in info])),
+                     "mean_iters": float(np.mean([f.iters for f in info])),
+                     "mean_rel_err": float(np.mean(errs)), "sampled_queries": len(errs)})
+        tree.close()
+        del out, flush
+    return rows
 
 
 def append_section(tk, torch, dev, local, n_app):

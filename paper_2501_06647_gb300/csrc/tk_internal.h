@@ -61,8 +61,7 @@ struct TkQueryBatch {
   void* out;               // device
   tk_query_info* info;     // device, n (may be null)
   const int* order;        // device, n: processing order (may be null: index order)
-  const int* split;        // device: number of leading entries of `order` in part 1
-  int part;                // 0: jobs [0, n); 1: jobs [0, *split); 2: jobs [*split, n)
+  const int* split;        // device (may be null): leading entries of `order` that are heavy
   int rq[TK_MAXP];         // requested ranks
   const int64_t* tq;       // device, n (may be null): the T each query is answered at
                            // (<= the tree's T; a query must not reach into that T's open block

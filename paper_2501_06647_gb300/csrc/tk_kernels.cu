@@ -775,15 +775,12 @@ __global__ void __launch_bounds__(2 * TK_NT) k_stitch(TkTreeView tv, int mode, i
   unsigned char* arena = smem_raw + align16(sizeof(WarpSm<S>));
   WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(gsm);
   S* ws = reinterpret_cast<S*>(wsd.base) + (int64_t)blockIdx.x * wsd.per_cta;
-  int job_lo = 0, job_hi = njobs;
-  if (qb.part == 1) job_hi = *qb.split;
-  if (qb.part == 2) job_lo = *qb.split;
   while (true) {
-    if (tid == 0) sm.job = job_lo + (int)atomicAdd(wsd.counter, 1u);
+    if (tid == 0) sm.job = (int)atomicAdd(wsd.counter, 1u);
     G::sync();
     const int job = sm.job;
     G::sync();
-    if (job >= job_hi) break;
+    if (job >= njobs) break;
     if (mode == TK_JOB_QUERY) {
       query_job<G, S>(tv, qb, qb.order ? qb.order[job] : job, ws, wsd.per_cta, wsd.smem_arena, wsd.status, gsm,
                       arena);
