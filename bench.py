@@ -333,13 +333,8 @@ def main():
     gpu_launches = tree.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
     n_q = len(Q)
-    value = world * n_q * args.steps / (total_ms / 1e3)
+    total_ms, value = replica_throughput(total_ms, n_q * args.steps, world, dist, dev)
     tree.sync()
 
     # ---- per-query latency: one query per launch (plain method) ------------------
@@ -568,6 +563,21 @@ def theta_sweep(tk, torch, dev, local, thetas=((1, 2), (7, 10), (9, 10))):
         tree.close()
         del out, flush
     return rows
+
+
+def replica_throughput(local_ms, local_units, world, dist=None, device=None):
+    """Whole-job throughput of N replicas (Section 7's queries are
+    independent: every rank answers its own copy of the batch, no data-path
+    collective).  The job's time is the slowest rank's (max over ranks, then
+    a barrier); value = all ranks' units / that time.  Returns (ms, units/s)."""
+    total_ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    return total_ms, world * local_units / (total_ms / 1e3)
 
 
 def append_section(tk, torch, dev, local, n_app):
