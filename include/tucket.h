@@ -167,12 +167,17 @@ int tk_tree_get_config(const tk_tree* t, tk_config* out);
  *
  * A server owns a worker thread that executes the requests submitted to it,
  * from any host thread, in ticket (arrival) order: a range query sees every
- * stream update submitted before it (Section 3's two operations, served
- * concurrently).  Queries waiting at the head of the queue are admitted into
- * one batched launch, up to max_batch queries and max_batch_out_elems output
- * elements (the device memory a batch may hold); the next batch is enqueued
- * while the current one runs, and appends are applied between batches.
- * While a server exists, the tree must not be used directly. */
+ * stream update submitted before it and none submitted after it (Section 3's
+ * two operations, served concurrently).  Appends are issued at once, in
+ * stream order behind the batches already running; an append's ticket
+ * completes when it has been issued.  Queries are admitted into one batched
+ * launch, up to max_batch queries and max_batch_out_elems output elements
+ * (the device memory a batch may hold), each answered against the tree as of
+ * its own submission (nodes complete then are never changed by later
+ * appends); a query that reaches into the open block of its time makes the
+ * batch launch before the next append.  The next batch is enqueued while
+ * the current one runs.  While a server exists, the tree must not be used
+ * directly. */
 typedef struct tk_server tk_server;
 typedef struct tk_server_config {
   int32_t max_batch;               /* queries per batch (default 1024) */
