@@ -1,7 +1,8 @@
 // Cooperative building blocks for the small dense linear algebra of a stitch
-// or leaf job.  Every routine is executed by all threads of a *group* -- one
-// warp (WarpGroup, the stitch kernel: one query per warp) or one CTA
-// (BlockGroup, the leaf kernel) -- works on plain pointers (shared or global
+// or leaf job.  Every routine is executed by all threads of a *group* -- a
+// whole CTA (BlockGroup: leaf CTAs, merge and single-query CTAs, heavy
+// queries of a batch) or one 256-thread half of a 512-thread CTA (HalfGroup:
+// light queries of a batch) -- works on plain pointers (shared or global
 // memory), uses a fixed reduction order (so repeated runs are bit-identical)
 // and ends with a group barrier.
 #pragma once
@@ -21,16 +22,6 @@ template <class S> __device__ __forceinline__ S warp_sum(S v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-
-// One warp.  Warp-synchronous: __syncwarp orders shared and global memory
-// among its lanes.
-struct WarpGroup {
-  static __device__ __forceinline__ int rank() { return threadIdx.x & 31; }
-  static __device__ __forceinline__ int size() { return 32; }
-  static __device__ __forceinline__ int nwarps() { return 1; }
-  static __device__ __forceinline__ void sync() { __syncwarp(); }
-  template <class S> static __device__ __forceinline__ S sum(S v, S*) { return warp_sum(v); }
-};
 
 // One CTA.  sum() needs >= 33 elements of shared scratch.
 struct BlockGroup {
