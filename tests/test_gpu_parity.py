@@ -230,3 +230,22 @@ def test_fp32_rank16_wide_slices_matches_fp64_oracle():
         rel, dist, ang, ee, eo = compare(X, int(ts), int(te), Ge, Ue, ro["G"], ro["U"])
         assert dist < 1e-3, (ts, te, dist)
         assert abs(ee - eo) < 1e-3 * max(eo, 0.1), (ts, te, ee, eo)
+
+
+def test_five_way_matches_fp64_oracle():
+    """A 5-way series (4 non-temporal modes): hit sets bit for bit, FP64
+    errors within 1e-9 relative and factor subspaces within 1e-3 rad, as for
+    the 3-way parity workload."""
+    dims, ranks = (6, 5, 4, 3), (3, 2, 2, 2, 2)
+    T, B = 48, 4
+    X = series(T, dims, ranks, 24, 0.01, 1005)
+    o = oracle_tree(X, dims, ranks, B, 3, 0.0)
+    e = engine_tree(X, dims, ranks, B, 3, 0.0, "f64")
+    for ts, te in synth.query_ranges(T, 12, 2005):
+        assert [tuple(h[:6]) for h in e.hit_set(int(ts), int(te))] == o.hit_records(int(ts), int(te))
+        ro = o.query(int(ts), int(te))
+        Ge, Ue, info = e.query(int(ts), int(te))
+        assert info["ranks"] == ro["ranks"]
+        rel, dist, ang, ee, eo = compare(X, int(ts), int(te), Ge, Ue, ro["G"], ro["U"])
+        assert rel < 1e-9, (ts, te, rel)
+        assert ang < 1e-3, (ts, te, ang)
