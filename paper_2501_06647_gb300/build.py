@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtucket.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tk_kernels.cu", "tk_leaf.cu", "tk_engine.cu", "tk_server.cu"]
+SOURCES = ["tk_kernels.cu", "tk_stitch_f32.cu", "tk_stitch_f64.cu", "tk_batch_f32.cu", "tk_batch_f64.cu",
+           "tk_leaf.cu", "tk_engine.cu", "tk_server.cu"]
 
 
 def nvcc_path():
