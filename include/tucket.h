@@ -47,7 +47,8 @@ typedef enum tk_status {
   TK_ERR_STATE = -6,       /* call not valid in the tree's current state */
   TK_ERR_WORKSPACE = -7,   /* device job exceeded its workspace (reported by tk_sync) */
   TK_ERR_TOO_BIG = -8,     /* request exceeds a fixed limit of the engine */
-  TK_ERR_TIMEOUT = -9      /* a wait ran out of time */
+  TK_ERR_TIMEOUT = -9,     /* a wait ran out of time */
+  TK_ERR_IO = -10          /* a tree file could not be read or written, or is not one */
 } tk_status;
 
 typedef enum tk_dtype { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
@@ -162,6 +163,34 @@ const char* tk_strerror(int code);
 
 /* Copy of the configuration the tree was created with. */
 int tk_tree_get_config(const tk_tree* t, tk_config* out);
+
+/* ---- Tree files (checkpoint and resume of a stream summary) --------------
+ *
+ * The tree is the stream's persistent summary (Section 4): after a restart a
+ * stream can resume from a saved tree instead of re-decomposing its history.
+ *
+ * tk_tree_save writes the tree to the file `path` (created or truncated):
+ * its configuration, its time span T, the node arena (the core, the factors
+ * of every mode, the temporal factor rows and the ranks of every stored
+ * node, including the open block's decomposition when it is current) and the
+ * raw slices of the open leaf block.  Synchronous: it first waits for the
+ * tree's stream and returns the first device-side error, if any, without
+ * writing.  The file holds the host's byte order and the element size and is
+ * read back only by tk_tree_load.  Not valid while a server uses the tree.
+ *
+ * tk_tree_load creates a tree from such a file, on `device` (-1: the device
+ * recorded in the file) and `cuda_stream` (as for tk_tree_create), and
+ * returns it in *out.  Its arena holds the saved bytes, so it answers every
+ * query and takes further appends exactly as the saved tree would.
+ * Synchronous.
+ *
+ * Both return TK_ERR_IO when the file cannot be opened, written or read, or
+ * is not a complete tree file of this format (wrong header, sizes that do
+ * not match its configuration, missing or trailing bytes); tk_tree_load
+ * also returns the errors of tk_tree_create.  On error tk_tree_load leaves
+ * *out NULL and frees what it created. */
+int tk_tree_save(tk_tree* t, const char* path);
+int tk_tree_load(const char* path, int device, void* cuda_stream, tk_tree** out);
 
 /* ---- Serving: continuous batching of queries and appends ---------------
  *

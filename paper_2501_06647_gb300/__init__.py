@@ -23,6 +23,7 @@ _ERR = {
     -4: "device allocation failed", -5: "CUDA runtime error", -6: "invalid tree state",
     -7: "device job exceeded its workspace", -8: "request exceeds an engine limit",
     -9: "a wait ran out of time",
+    -10: "tree file could not be read or written, or is not a tree file",
 }
 
 
@@ -85,6 +86,9 @@ _SIGS = {
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p]),
     "tk_tree_get_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TkConfig)]),
+    "tk_tree_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "tk_tree_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_void_p)]),
     "tk_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TkServerConfig),
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "tk_server_submit_query": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -174,6 +178,31 @@ class Tree:
         _check(lib().tk_tree_create(ctypes.byref(cfg), s, ctypes.byref(h)), "tk_tree_create")
         self.h = h
         self.B = int(leaf_slices)
+
+    def save(self, path):
+        """Write the tree to a file (tk_tree_save; synchronous)."""
+        _check(lib().tk_tree_save(self.h, os.fsencode(path)), "tk_tree_save")
+
+    @classmethod
+    def load(cls, path, device=None, stream=None):
+        """A tree read from a file written by save() (tk_tree_load), on `device`
+        (default: the device recorded in the file)."""
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
+        _check(lib().tk_tree_load(os.fsencode(path), -1 if device is None else int(device), s, ctypes.byref(h)),
+               "tk_tree_load")
+        self = cls.__new__(cls)
+        self.h = h
+        cfg = TkConfig()
+        _check(lib().tk_tree_get_config(h, ctypes.byref(cfg)), "tk_tree_get_config")
+        self.cfg = cfg
+        self.p = int(cfg.p)
+        self.dims = tuple(int(cfg.dims[n]) for n in range(1, self.p))
+        self.ranks = tuple(int(cfg.ranks[n]) for n in range(self.p))
+        self.dtype = "f64" if cfg.dtype == TK_F64 else "f32"
+        self.np_dtype = _np_dtype(self.dtype)
+        self.B = int(cfg.leaf_slices)
+        return self
 
     def close(self):
         if getattr(self, "h", None):

@@ -550,6 +550,7 @@ const char* tk_strerror(int code) {
     case TK_ERR_WORKSPACE: return "device job exceeded its workspace or hit limit";
     case TK_ERR_TOO_BIG: return "request exceeds a fixed engine limit";
     case TK_ERR_TIMEOUT: return "a wait ran out of time";
+    case TK_ERR_IO: return "tree file could not be read or written, or is not a tree file";
     default: return "unknown error";
   }
 }
@@ -1022,5 +1023,174 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
   if (rc) return rc;
   if (st == TK_DEV_ERR_RANGE) return TK_ERR_RANGE;
   if (st != 0) return TK_ERR_WORKSPACE;
+  return TK_OK;
+}
+
+// ---- Tree files --------------------------------------------------------------
+// A saved tree is its configuration and time span followed by the device
+// buffers that hold its state, byte for byte: the node arena (cores, the
+// non-temporal factors of every mode, the temporal factor rows of every level,
+// the node ranks) and the raw slices of the open leaf block.  The arena layout
+// is a function of the block capacity alone, so a tree created with the saved
+// configuration and grown to the saved capacity has buffers of the same sizes
+// and layout, and copying the bytes back restores the tree exactly.
+namespace {
+
+constexpr char kFileMagic[8] = {'T', 'K', 'T', 'R', 'E', 'E', '\0', '\1'};
+constexpr int kFileSections = 4 + TK_MAXP;
+
+struct TkFileHeader {
+  char magic[8];
+  uint32_t header_bytes;  // sizeof(TkFileHeader): catches a different build of this struct
+  uint32_t elem_bytes;    // 4 or 8
+  tk_config cfg;
+  int64_t T, nb, nbcap;
+  int32_t tail_dirty;
+  int32_t nsec;
+  int64_t sec_bytes[kFileSections];
+};
+
+// The buffers of a file, in file order: core pool, temporal factor rows, node
+// ranks, open-block slices, then the factor pool of each mode (mode 0 and the
+// modes beyond p have none: zero bytes).
+void file_sections(tk_tree* t, DevBuf** s) {
+  s[0] = &t->core_pool;
+  s[1] = &t->tfac;
+  s[2] = &t->node_ranks;
+  s[3] = &t->tail_raw;
+  for (int n = 0; n < TK_MAXP; ++n) s[4 + n] = &t->fac_pool[n];
+}
+
+constexpr size_t kFileChunk = (size_t)64 << 20;
+
+int section_out(tk_tree* t, const DevBuf& b, FILE* f, std::vector<char>& stage) {
+  for (size_t done = 0; done < b.bytes;) {
+    const size_t c = std::min(stage.size(), b.bytes - done);
+    if (cudaMemcpyAsync(stage.data(), (const char*)b.ptr + done, c, cudaMemcpyDeviceToHost, t->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(t->stream) != cudaSuccess)
+      return TK_ERR_CUDA;
+    if (std::fwrite(stage.data(), 1, c, f) != c) return TK_ERR_IO;
+    done += c;
+  }
+  return TK_OK;
+}
+
+int section_in(tk_tree* t, DevBuf& b, FILE* f, std::vector<char>& stage) {
+  for (size_t done = 0; done < b.bytes;) {
+    const size_t c = std::min(stage.size(), b.bytes - done);
+    if (std::fread(stage.data(), 1, c, f) != c) return TK_ERR_IO;
+    if (cudaMemcpyAsync((char*)b.ptr + done, stage.data(), c, cudaMemcpyHostToDevice, t->stream) != cudaSuccess ||
+        cudaStreamSynchronize(t->stream) != cudaSuccess)
+      return TK_ERR_CUDA;
+    done += c;
+  }
+  return TK_OK;
+}
+
+// Header fields that must hold before any device work.
+bool header_plausible(const TkFileHeader& h) {
+  if (std::memcmp(h.magic, kFileMagic, sizeof(kFileMagic)) != 0) return false;
+  if (h.header_bytes != sizeof(TkFileHeader) || h.nsec != kFileSections) return false;
+  if (h.cfg.dtype != TK_F64 && h.cfg.dtype != TK_F32) return false;
+  if (h.elem_bytes != (h.cfg.dtype == TK_F64 ? 8u : 4u)) return false;
+  const int64_t B = h.cfg.leaf_slices;
+  if (B < 1 || h.T < 0 || h.nb != h.T / B) return false;
+  if (h.nbcap < 1 || (h.nbcap & (h.nbcap - 1)) != 0 || h.nbcap < (h.T + B - 1) / B) return false;
+  if (h.tail_dirty != 0 && h.tail_dirty != 1) return false;
+  for (int i = 0; i < kFileSections; ++i)
+    if (h.sec_bytes[i] < 0) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" int tk_tree_save(tk_tree* t, const char* path) {
+  if (!t || !path) return TK_ERR_ARG;
+  DeviceGuard g(t->dev);
+  int rc = tk_sync(t);  // pending work first; a device-side error is reported, nothing is written
+  if (rc) return rc;
+  TkFileHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kFileMagic, sizeof(kFileMagic));
+  h.header_bytes = sizeof(TkFileHeader);
+  h.elem_bytes = (uint32_t)t->es;
+  h.cfg = t->cfg;
+  h.T = t->T;
+  h.nb = t->nb;
+  h.nbcap = t->nbcap;
+  h.tail_dirty = t->tail_dirty ? 1 : 0;
+  h.nsec = kFileSections;
+  DevBuf* s[kFileSections];
+  file_sections(t, s);
+  size_t largest = 0;
+  for (int i = 0; i < kFileSections; ++i) {
+    h.sec_bytes[i] = (int64_t)s[i]->bytes;
+    largest = std::max(largest, s[i]->bytes);
+  }
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return TK_ERR_IO;
+  std::vector<char> stage;
+  try {
+    stage.resize(std::max<size_t>(1, std::min(largest, kFileChunk)));
+  } catch (...) {
+    std::fclose(f);
+    return TK_ERR_NOMEM;
+  }
+  rc = std::fwrite(&h, sizeof(h), 1, f) == 1 ? TK_OK : TK_ERR_IO;
+  for (int i = 0; i < kFileSections && rc == TK_OK; ++i) rc = section_out(t, *s[i], f, stage);
+  if (std::fclose(f) != 0 && rc == TK_OK) rc = TK_ERR_IO;
+  return rc;
+}
+
+extern "C" int tk_tree_load(const char* path, int device, void* cuda_stream, tk_tree** out) {
+  if (!path || !out) return TK_ERR_ARG;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return TK_ERR_IO;
+  TkFileHeader h;
+  if (std::fread(&h, sizeof(h), 1, f) != 1 || !header_plausible(h)) {
+    std::fclose(f);
+    return TK_ERR_IO;
+  }
+  tk_config cfg = h.cfg;
+  if (device >= 0) cfg.device = device;
+  tk_tree* t = nullptr;
+  int rc = tk_tree_create(&cfg, cuda_stream, &t);
+  if (rc) {
+    std::fclose(f);
+    return rc;
+  }
+  {
+    DeviceGuard g(t->dev);
+    rc = ensure_capacity(t, h.nbcap);
+    if (rc == TK_OK && t->nbcap != h.nbcap) rc = TK_ERR_IO;
+    DevBuf* s[kFileSections];
+    file_sections(t, s);
+    size_t largest = 0;
+    for (int i = 0; i < kFileSections && rc == TK_OK; ++i) {
+      if ((int64_t)s[i]->bytes != h.sec_bytes[i]) rc = TK_ERR_IO;
+      largest = std::max(largest, s[i]->bytes);
+    }
+    std::vector<char> stage;
+    if (rc == TK_OK) {
+      try {
+        stage.resize(std::max<size_t>(1, std::min(largest, kFileChunk)));
+      } catch (...) {
+        rc = TK_ERR_NOMEM;
+      }
+    }
+    for (int i = 0; i < kFileSections && rc == TK_OK; ++i) rc = section_in(t, *s[i], f, stage);
+    if (rc == TK_OK && std::fgetc(f) != EOF) rc = TK_ERR_IO;  // trailing bytes: not a file of this tree
+  }
+  std::fclose(f);
+  if (rc) {
+    tk_tree_destroy(t);
+    return rc;
+  }
+  t->T = h.T;
+  t->nb = h.nb;
+  t->tail_dirty = h.tail_dirty != 0;
+  *out = t;
   return TK_OK;
 }

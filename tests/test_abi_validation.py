@@ -3,13 +3,14 @@ through ctypes on a CPU host: every check here runs before the library
 touches a device, so no GPU is needed.  A call that fails validation must
 return its error code and change nothing."""
 import ctypes
+import os
 
 import pytest
 
 import paper_2501_06647_gb300 as tk
 from paper_2501_06647_gb300 import build as b
 
-ARG, RANGE, RANK, CUDA = -1, -2, -3, -5
+ARG, RANGE, RANK, CUDA, IO = -1, -2, -3, -5, -10
 
 
 @pytest.fixture(scope="module")
@@ -71,12 +72,15 @@ def test_null_arguments(lib):
     assert lib.tk_server_submit_append(None, None, None) == ARG
     assert lib.tk_server_wait(None, 1, 0.0) == ARG
     assert lib.tk_server_drain(None, 0.0) == ARG
+    assert lib.tk_tree_save(None, b"x") == ARG
+    assert lib.tk_tree_load(None, -1, None, ctypes.byref(sh)) == ARG
+    assert lib.tk_tree_load(b"x", -1, None, None) == ARG
     lib.tk_tree_destroy(None)   # no-ops
     lib.tk_server_destroy(None)
 
 
 def test_every_status_has_a_message(lib):
-    msgs = [lib.tk_strerror(code) for code in range(0, -10, -1)]
+    msgs = [lib.tk_strerror(code) for code in range(0, -11, -1)]
     assert all(m for m in msgs) and len(set(msgs)) == len(msgs)
 
 
@@ -90,3 +94,63 @@ def test_valid_configuration_without_a_device_reports_cuda():
     h = ctypes.c_void_p()
     assert lib.tk_tree_create(ctypes.byref(c), None, ctypes.byref(h)) == CUDA
     assert h.value is None
+
+
+class _FileHeader(ctypes.Structure):
+    """The fixed header of a tree file, as tk_tree_save writes it."""
+    _fields_ = [("magic", ctypes.c_char * 8), ("header_bytes", ctypes.c_uint32), ("elem_bytes", ctypes.c_uint32),
+                ("cfg", tk.TkConfig), ("T", ctypes.c_int64), ("nb", ctypes.c_int64), ("nbcap", ctypes.c_int64),
+                ("tail_dirty", ctypes.c_int32), ("nsec", ctypes.c_int32),
+                ("sec_bytes", ctypes.c_int64 * (4 + tk.MAX_MODES))]
+
+
+def _header(lib, magic=b"TKTREE\x00\x01", **kw):
+    h = _FileHeader()
+    h.header_bytes = ctypes.sizeof(_FileHeader)
+    h.cfg = _cfg(lib, leaf_slices=4)
+    h.elem_bytes = 4
+    h.T, h.nb, h.nbcap, h.tail_dirty, h.nsec = 50, 12, 16, 1, 4 + tk.MAX_MODES
+    for k, v in kw.items():
+        setattr(h, k, v)
+    # (a c_char array field stops copying at the first NUL: set the magic bytes directly)
+    return magic + bytes(h)[8:]
+
+
+def _load(lib, path):
+    h = ctypes.c_void_p(1234)
+    rc = lib.tk_tree_load(os.fsencode(path), -1, None, ctypes.byref(h))
+    assert h.value is None  # nothing returned on failure
+    return rc
+
+
+def test_files_that_are_not_tree_files_are_rejected(lib, tmp_path):
+    """Checked from the header alone, before any device work."""
+    assert _load(lib, tmp_path / "missing.tkt") == IO
+    f = tmp_path / "bad.tkt"
+    good = _header(lib)
+    bad = [b"", b"not a tree file", good[:40],                      # empty, garbage, truncated header
+           _header(lib, magic=b"TKTREE\x00\x02"),                  # another format version
+           _header(lib, header_bytes=8), _header(lib, nsec=3),       # another header layout
+           _header(lib, elem_bytes=8),                               # element size not the dtype's
+           _header(lib, nb=11),                                      # nb != T / B
+           _header(lib, nbcap=12), _header(lib, nbcap=8),            # capacity not a power of two / too small
+           _header(lib, T=-1, nb=0), _header(lib, tail_dirty=2)]
+    for content in bad:
+        f.write_bytes(content)
+        assert _load(lib, f) == IO, content[:16]
+
+
+def test_a_plausible_header_reaches_tree_creation():
+    """A header that passes every check goes on to create the tree: without a
+    device that is where it stops, with TK_ERR_CUDA."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the load would go on to read the sections")
+    import tempfile
+    b.build()
+    lib = tk.lib()
+    with tempfile.TemporaryDirectory() as d:
+        f = os.path.join(d, "h.tkt")
+        with open(f, "wb") as fh:
+            fh.write(_header(lib))
+        assert _load(lib, f) == CUDA
