@@ -68,6 +68,33 @@ def test_stitch_equals_dense_hooi_on_stitched_tensor(iters):
         assert np.abs(u.T @ u - np.eye(u.shape[1])).max() < 1e-12
 
 
+@pytest.mark.parametrize("p", [4, 5, 6, 7])
+def test_more_modes_match_the_materialized_tensor(p):
+    # The paper's mode-count experiment reaches p = 7 (Section 8, synthetic
+    # tensors); with p >= 4 a wrong Kronecker order of the non-temporal modes
+    # in Eq. (stitch-temp-2) / Eq. (stitch-nontemp-3) changes the result.
+    rng = np.random.default_rng(40 + p)
+    dims = tuple(int(d) for d in rng.integers(3, 6, size=p - 1))
+    q = (3,) + (2,) * (p - 1)
+    hits = _rand_hits(50 + p, [4, 3, 5], dims, q)
+    Y = stitch.materialize_stitched(hits)
+    U = [_rand_orth(rng, Y.shape[0], 3)] + [_rand_orth(rng, d, 2) for d in dims]
+    ref1 = tensor.unfold(tensor.multi_mode_product(Y, [None] + [u.T for u in U[1:]]), 0)
+    assert np.allclose(stitch.temporal_matricization(hits, U), ref1, atol=1e-12)
+    offs = np.cumsum([0] + [V[0].shape[0] for _, V in hits])
+    for n in range(1, p):
+        mats = [u.T for u in U]
+        mats[n] = None
+        ref = tensor.unfold(tensor.multi_mode_product(Y, mats), n)
+        assert np.allclose(stitch.nontemporal_matricization(hits, U, n, offs), ref, atol=1e-12)
+    r = stitch.stitched_ranks(hits, dims, (3,) + (2,) * (p - 1))
+    G, Us, it, errs = stitch.stitch(hits, r, max_iter=2, tol=0)
+    Gd, Ud, itd, errsd = hooi.tucker_als(Y, r, max_iter=2, tol=0)
+    assert it == itd == 2
+    assert metrics.model_distance(G, Us, Gd, Ud) < 1e-10 * tensor.frob(Y)
+    assert abs(errs[-1] - errsd[-1]) < 1e-12
+
+
 def test_full_rank_stitch_is_exact():
     hits = _rand_hits(4, [3, 2, 4], (4, 3), (2, 2, 2))
     Y = stitch.materialize_stitched(hits)
