@@ -136,9 +136,11 @@ def _np_dtype(dtype):
 def _ptr(x):
     """Address of a torch tensor or numpy array (contiguous)."""
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous()
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
         return ctypes.c_void_p(x.data_ptr())
-    assert x.flags["C_CONTIGUOUS"]
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
     return ctypes.c_void_p(x.ctypes.data)
 
 
