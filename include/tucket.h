@@ -66,6 +66,7 @@ typedef struct tk_config {
   double tol;                       /* stop when |e_k - e_{k-1}| < tol; <= 0: run max_iter */
   int32_t dtype;                    /* tk_dtype */
   int32_t device;                   /* CUDA device ordinal */
+  int64_t hbm_budget;               /* device bytes the tree may hold (0: no limit) */
 } tk_config;
 
 /* One node of a hit set (Algorithm 1, Section 5.1), in time order. */
@@ -93,11 +94,19 @@ typedef struct tk_query_info {
 typedef struct tk_tree tk_tree;
 
 /* Fill *cfg with defaults: p = 3, ranks 10, B = 1, theta = 7/10,
- * max_iter = 20, tol = 0.01, TK_F32, device 0.  dims must still be set. */
+ * max_iter = 20, tol = 0.01, TK_F32, device 0, no memory budget.  dims must
+ * still be set. */
 int tk_config_default(tk_config* cfg);
 
 /* Create an empty tree (T = 0) on cfg->device.  cuda_stream is a
- * cudaStream_t to run on, or NULL for a stream the tree creates and owns. */
+ * cudaStream_t to run on, or NULL for a stream the tree creates and owns.
+ *
+ * Memory budget: with cfg->hbm_budget > 0, every call that would take the
+ * device bytes the tree holds (node arena, workspaces, staging buffers,
+ * the open block's slices) above the budget returns TK_ERR_NOMEM before
+ * changing anything; so does tk_tree_create when the empty tree does not fit.
+ * Not counted: the moment an arena that grows holds its old and new copies
+ * together, and a server's own buffers (sized by tk_server_config). */
 int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out);
 void tk_tree_destroy(tk_tree* t);
 

@@ -101,6 +101,31 @@ struct DeviceGuard {
   }
 };
 
+// Device bytes the tree holds in its own buffers.
+size_t held_bytes(const tk_tree* t) {
+  const DevBuf* bufs[] = {&t->core_pool, &t->tfac, &t->node_ranks, &t->tail_raw, &t->ws_stitch, &t->ws_leaf,
+                          &t->status, &t->stage_in, &t->stage_out, &t->stage_meta, &t->stage_info,
+                          &t->hit_buf, &t->plan};
+  size_t b = 0;
+  for (const DevBuf* x : bufs) b += x->bytes;
+  for (int n = 0; n < TK_MAXP; ++n) b += t->fac_pool[n].bytes;
+  return b;
+}
+
+// True when the tree may hold `add` more bytes after releasing `drop`
+// (cfg.hbm_budget, 0 = no limit).
+bool within_budget(const tk_tree* t, size_t drop, size_t add) {
+  if (t->cfg.hbm_budget <= 0) return true;
+  return held_bytes(t) - drop + add <= (size_t)t->cfg.hbm_budget;
+}
+
+// dalloc of one of the tree's buffers (or a temporary of a call) under the budget.
+int tdalloc(tk_tree* t, DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.ptr) return TK_OK;
+  if (!within_budget(t, b.bytes, bytes)) return TK_ERR_NOMEM;
+  return dalloc(b, bytes);
+}
+
 int64_t nbt_of(const tk_tree* t) { return (t->T + t->cfg.leaf_slices - 1) / t->cfg.leaf_slices; }
 
 TkTreeView make_view(const tk_tree* t) {
@@ -165,6 +190,14 @@ int ensure_capacity(tk_tree* t, int64_t need_blocks) {
   const size_t es = t->es;
   const int r0 = t->cfg.ranks[0];
   const int64_t Tcap_new = ncap * t->cfg.leaf_slices;
+  {
+    size_t old_arena = t->core_pool.bytes + t->tfac.bytes + t->node_ranks.bytes, new_arena = 0;
+    for (int n = 0; n < TK_MAXP; ++n) old_arena += t->fac_pool[n].bytes;
+    new_arena += (size_t)L.nslots * t->core_stride * es;
+    for (int n = 1; n < p; ++n) new_arena += (size_t)L.nslots * t->fac_stride[n] * es;
+    new_arena += (size_t)L.nlevels * Tcap_new * r0 * es + (size_t)L.nslots * TK_MAXP * sizeof(int);
+    if (!within_budget(t, old_arena, new_arena)) return TK_ERR_NOMEM;
+  }
   DevBuf core, fac[TK_MAXP], tf, nr;
   int rc = dalloc(core, (size_t)L.nslots * t->core_stride * es);
   for (int n = 1; n < p && rc == TK_OK; ++n) rc = dalloc(fac[n], (size_t)L.nslots * t->fac_stride[n] * es);
@@ -371,7 +404,7 @@ int ensure_ws_stitch(tk_tree* t, int want_ctas) {
   int ctas = std::max(1, want_ctas);
   if (per != t->ws_stitch_per_cta || ctas > t->ws_stitch_ctas) {
     ctas = std::max(ctas, t->ws_stitch_ctas);
-    const int rc = dalloc(t->ws_stitch, (size_t)per * ctas * t->es);
+    const int rc = tdalloc(t, t->ws_stitch, (size_t)per * ctas * t->es);
     if (rc) return rc;
     t->ws_stitch_per_cta = per;
     t->ws_stitch_ctas = ctas;
@@ -387,7 +420,7 @@ int ensure_ws_leaf(tk_tree* t, int want_clusters, TkLeafLayout* ly) {
   int n = std::max(1, want_clusters);
   if (per != t->ws_leaf_per_cta || n > t->ws_leaf_ctas) {
     n = std::max(n, t->ws_leaf_ctas);
-    const int rc = dalloc(t->ws_leaf, (size_t)per * n * t->es);
+    const int rc = tdalloc(t, t->ws_leaf, (size_t)per * n * t->es);
     if (rc) return rc;
     t->ws_leaf_per_cta = per;
     t->ws_leaf_ctas = n;
@@ -511,7 +544,7 @@ int launch_batch(tk_tree* t, int n, const int64_t* d_ranges, const int64_t* d_of
     // light rest in two halves (see k_batch).
     const int bgrid = std::min(n, t->sm_count);
     const int64_t per = stitch_ws_bound(t, max_hits(t, t->nbcap));
-    rc = dalloc(t->plan, sizeof(int) * ((size_t)n + 4));
+    rc = tdalloc(t, t->plan, sizeof(int) * ((size_t)n + 4));
     if (rc == TK_OK) rc = ensure_ws_stitch(t, 2 * bgrid);
     if (rc) return rc;
     int* split = (int*)t->plan.ptr;
@@ -577,6 +610,7 @@ int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out) {
   if (cfg->leaf_slices < 1 || cfg->theta_den < 1 || cfg->theta_num < 1 || cfg->theta_num > cfg->theta_den)
     return TK_ERR_ARG;
   if (cfg->max_iter < 1 || (cfg->dtype != TK_F64 && cfg->dtype != TK_F32)) return TK_ERR_ARG;
+  if (cfg->hbm_budget < 0) return TK_ERR_ARG;
   for (int n = 0; n < cfg->p; ++n)
     if (cfg->ranks[n] < 1 || cfg->ranks[n] > 4096) return TK_ERR_ARG;
   for (int n = 1; n < cfg->p; ++n)
@@ -608,8 +642,8 @@ int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out) {
   t->core_stride = 1;
   for (int n = 0; n < t->p; ++n) t->core_stride *= cfg->ranks[n];
   for (int n = 1; n < t->p; ++n) t->fac_stride[n] = cfg->dims[n] * cfg->ranks[n];
-  int rc = dalloc(t->tail_raw, (size_t)cfg->leaf_slices * t->slice_elems * t->es);
-  if (rc == TK_OK) rc = dalloc(t->status, 64);
+  int rc = tdalloc(t, t->tail_raw, (size_t)cfg->leaf_slices * t->slice_elems * t->es);
+  if (rc == TK_OK) rc = tdalloc(t, t->status, 64);
   if (rc == TK_OK) rc = cuda_ok(cudaMemsetAsync(t->status.ptr, 0, 64, t->stream));
   if (rc == TK_OK) rc = ensure_capacity(t, 1);
   if (rc != TK_OK) {
@@ -671,7 +705,7 @@ int tk_tree_build(tk_tree* t, const void* X, int64_t T, int io) {
   const void* Xd = X;
   DevBuf tmp;
   if (io == TK_IO_HOST) {
-    rc = dalloc(tmp, (size_t)T * t->slice_elems * t->es);
+    rc = tdalloc(t, tmp, (size_t)T * t->slice_elems * t->es);
     if (rc) return rc;
     rc = cuda_ok(cudaMemcpyAsync(tmp.ptr, X, tmp.bytes, cudaMemcpyHostToDevice, t->stream));
     if (rc) {
@@ -737,7 +771,7 @@ int tk_hit_set(tk_tree* t, int64_t t_s, int64_t t_e, tk_hit* out, int cap, int* 
   if (!(t_s >= 0 && t_s < t_e && t_e <= t->T)) return TK_ERR_RANGE;
   DeviceGuard g(t->dev);
   const size_t need = 64 + sizeof(int64_t) * 2 + sizeof(tk_hit) * TK_MAXH;
-  int rc = dalloc(t->hit_buf, need);
+  int rc = tdalloc(t, t->hit_buf, need);
   if (rc) return rc;
   int64_t rng[2] = {t_s, t_e};
   char* base = (char*)t->hit_buf.ptr;
@@ -806,9 +840,9 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
   void* d_out = out;
   if (io == TK_IO_HOST) {
     const size_t meta = sizeof(int64_t) * (2 * (size_t)n + n + 1);
-    rc = dalloc(t->stage_meta, meta);
+    rc = tdalloc(t, t->stage_meta, meta);
     if (rc) return rc;
-    rc = dalloc(t->stage_out, (size_t)offsets[n] * t->es);
+    rc = tdalloc(t, t->stage_out, (size_t)offsets[n] * t->es);
     if (rc) return rc;
     int64_t* m = (int64_t*)t->stage_meta.ptr;
     rc = cuda_ok(cudaMemcpyAsync(m, ranges, sizeof(int64_t) * 2 * n, cudaMemcpyHostToDevice, t->stream));
@@ -821,7 +855,7 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
   }
   tk_query_info* d_info = nullptr;
   if (info) {
-    rc = dalloc(t->stage_info, sizeof(tk_query_info) * n);
+    rc = tdalloc(t, t->stage_info, sizeof(tk_query_info) * n);
     if (rc) return rc;
     d_info = (tk_query_info*)t->stage_info.ptr;
   }
@@ -884,7 +918,7 @@ int tk_range_query(tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks, v
   DeviceGuard g(t->dev);
   if (io == TK_IO_HOST) return tk_range_query_batch(t, 1, rng, offs, ranks, out, info, TK_IO_HOST);
   // device output: the two small arrays go through the metadata staging buffer
-  rc = dalloc(t->stage_meta, std::max<size_t>(t->stage_meta.bytes, sizeof(int64_t) * 4));
+  rc = tdalloc(t, t->stage_meta, std::max<size_t>(t->stage_meta.bytes, sizeof(int64_t) * 4));
   if (rc) return rc;
   int64_t* m = (int64_t*)t->stage_meta.ptr;
   int64_t hm[4] = {t_s, t_e, 0, offs[1]};

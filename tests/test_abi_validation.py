@@ -39,12 +39,13 @@ def test_defaults_follow_the_paper(lib):
     # Section 8.1: at most 20 ALS iterations, tolerance 0.01, theta = 0.7
     assert (c.p, c.max_iter, c.theta_num, c.theta_den, c.leaf_slices) == (3, 20, 7, 10, 1)
     assert abs(c.tol - 0.01) < 1e-15 and c.dtype == tk.TK_F32 and list(c.ranks[:3]) == [10, 10, 10]
+    assert c.hbm_budget == 0  # no memory budget
     assert lib.tk_config_default(None) == ARG
 
 
 @pytest.mark.parametrize("bad", [dict(p=1), dict(p=7), dict(leaf_slices=0), dict(theta_num=8, theta_den=7),
                                  dict(theta_den=0), dict(theta_num=0), dict(max_iter=0), dict(dtype=5),
-                                 dict(ranks0=0), dict(ranks0=5000), dict(dims1=0)])
+                                 dict(ranks0=0), dict(ranks0=5000), dict(dims1=0), dict(hbm_budget=-1)])
 def test_invalid_configurations_are_rejected(lib, bad):
     c = _cfg(lib, **bad)
     h = ctypes.c_void_p(1234)
