@@ -256,6 +256,8 @@ def main():
                     help="single-slice appends timed on the 4-way stream (0: skip)")
     ap.add_argument("--theta-sweep", action="store_true",
                     help="run only the pruning-threshold sweep (theta 0.5, 0.7, 0.9) and print it")
+    ap.add_argument("--latency-vs-T", action="store_true",
+                    help="run only the query-latency-versus-timespan series and print it")
     ap.add_argument("--appends-only", action="store_true",
                     help="run only the append-latency section and print it")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
@@ -273,6 +275,10 @@ def main():
     if args.theta_sweep:
         torch.cuda.set_device(0)
         print(json.dumps({"theta_sweep": theta_sweep(tk, torch, torch.device("cuda", 0), 0)}))
+        return 0
+    if args.latency_vs_T:
+        torch.cuda.set_device(0)
+        print(json.dumps({"latency_vs_T": latency_vs_T_section(tk, torch, torch.device("cuda", 0), 0)}))
         return 0
     if args.appends_only:
         torch.cuda.set_device(0)
@@ -639,6 +645,53 @@ def append_section(tk, torch, dev, local, n_app):
         "open_block_query_ms": {"mean": float(np.mean(tail)) if tail else None, "p99": q(tail, 0.99),
                                 "what": "query over the last 40 slices, decomposing the open block first"},
     }
+
+
+def latency_vs_T_section(tk, torch, dev, local, L=384, n_q=50, checkpoints=(512, 1024, 2048, 4096)):
+    """Query latency against the timespan T (the paper's experiment on
+    efficiency w.r.t. T): queries of one fixed length L, while single-slice
+    appends grow the stream between the measurements.  The FP32 plain
+    workload's series (100x100 slices, ranks 10, leaf 16): the tree is built
+    to the first checkpoint, then slices are appended one at a time up to
+    each next one; at every checkpoint n_q queries [s, s + L) with a uniform
+    start are answered one per launch, each timed with CUDA events on the
+    tree's stream."""
+    w = synth.WORKLOADS["fp32_plain"]
+    T_end = max(checkpoints)
+    X = synth.piecewise_tucker(T_end, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    stream = torch.cuda.Stream(device=dev)
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local,
+                   stream=stream)
+    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+    tree.build(Xd[:checkpoints[0]])
+    tree.sync()
+    rng = np.random.default_rng(w["qseed"])
+    points = []
+    for Tc in checkpoints:
+        while tree.T < Tc:
+            tree.append(Xd[tree.T])
+        tree.sync()
+        starts = rng.integers(0, Tc - L + 1, size=n_q)
+        ms, hits = [], []
+        for s0 in starts:
+            r = np.array([[s0, s0 + L]], dtype=np.int64)
+            o = tree.layout(r)
+            rd, od = torch.from_numpy(r).to(dev), torch.from_numpy(o).to(dev)
+            out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.query_batch(rd, od, out)
+            b.record(stream)
+            tree.sync()
+            ms.append(a.elapsed_time(b))
+            hits.append(len(tree.hit_set(int(s0), int(s0 + L))))
+        points.append({"T": int(Tc), "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                       "mean_hits": float(np.mean(hits))})
+    tree.close()
+    return {"workload": f"{w['dims'][0]}x{w['dims'][1]} slices, ranks {tuple(w['ranks'])}, leaf {w['B']}, FP32, "
+                        f"tol 0.01; built to T={checkpoints[0]}, then single-slice appends",
+            "query_length": L, "queries_per_point": n_q, "points": points}
 
 
 def serving_section(tk, torch, dev, local, seconds):
