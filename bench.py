@@ -46,7 +46,7 @@ def workload_desc(w):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic FLOPs of one query in the coefficient-space form
+# algorithmic FLOPs of one query in the coefficient-space form of the engine
 # ---------------------------------------------------------------------------
 def query_flops(hits, ranks_out, node_ranks, dims, iters):
     """FLOPs of one range query: partial-hit QR, QR of the stacked factors,

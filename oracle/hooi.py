@@ -5,7 +5,7 @@ Section 2: Tucker decomposition minimizes ||G x_1 U1 ... x_p Up - X||_F^2
 leading left singular vectors of mat_n(X x_{m!=n} U^(m)T) (Eq. (als-mat)), and
 the optimal core is X x_n U^(n)T over all modes.
 
-Readings the paper leaves open (listed in the design doc):
+Readings of what the paper leaves open:
   * ranks are clamped per mode: r_n' = min(r_n, D_n), then repeatedly
     r_n' = min(r_n', prod_{m!=n} r_m') until nothing changes, so that every
     matricization has at least r_n' columns;

@@ -7,7 +7,7 @@ Eq. (stitch-nontemp-3) write them, and takes LAPACK SVDs of them.
 A hit decomposition is a pair (H, V): core H (q_1 x ... x q_p) and factors
 V[0] (temporal, l x q_1, orthonormal columns) and V[n] (D_n x q_n, orthonormal).
 
-Readings (listed in DESIGN.md):
+Readings of what the paper leaves open:
   * the offsets t_i of Algorithm 2 are prefix sums of the CLIPPED lengths
     |[T_s,T_e) cap [sigma_v, tau_v)|, so that t_s = L;
   * "randomly initialize U^(2..p)" is replaced by the implicit HOSVD of the

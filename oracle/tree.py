@@ -6,7 +6,7 @@ Node kinds (Section 4.2): leaf 'L', intermediate 'M', placeholder 'P'.  Node
 ranges are kept in LEAF-BLOCK units; a leaf block is ``B`` consecutive slices
 (B = 1 is the paper's tree exactly).
 
-Readings (listed in DESIGN.md):
+Readings of what the paper leaves open:
   * Leaf blocks.  The tree of Algorithms 3/4 is built over blocks of B slices;
     a leaf's payload is Tucker-ALS (``hooi.tucker_als``) of its raw block.
   * Open block.  When the first slice of block b arrives, Algorithm 4 (root
