@@ -13,30 +13,20 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
 class _Structural(StreamSegmentTree):
-    """Tree with trivial payloads: only the structure and Recall are exercised."""
+    """The oracle's own tree (its Algorithm 3/4 descent and Recall), with only
+    the payload arithmetic stubbed: leaves get no decomposition, and the
+    module's Stitch and rank clamp are replaced by dummies (autouse fixture
+    below), so these pins check the real ``_insert`` / ``append`` code."""
 
     def _leaf_payload(self, block):
         return None, None
 
-    def _insert(self, v, b, complete):
-        # Same descent as Algorithm 3, with Stitch replaced by a counter.
-        if v.sigma == b and v.tau == b + 1:
-            v.kind = 'L'
-            return v
-        mu = (v.sigma + v.tau) // 2
-        if b < mu:
-            if v.left is None:
-                from oracle.tree import Node
-                v.left = Node(v.sigma, mu, 'P')
-            return self._insert(v.left, b, complete)
-        if v.right is None:
-            from oracle.tree import Node
-            v.right = Node(mu, v.tau, 'P')
-        leaf = self._insert(v.right, b, complete)
-        if complete and v.tau == b + 1:
-            v.kind = 'M'
-            self.stitch_count += 1
-        return leaf
+
+@pytest.fixture(autouse=True)
+def _no_payload_arithmetic(monkeypatch):
+    import oracle.tree as ot
+    monkeypatch.setattr(ot, "stitch", lambda hits, r, max_iter, tol: (None, None, 0, []))
+    monkeypatch.setattr(ot, "stitched_ranks", lambda hits, dims, ranks: None)
 
 
 def _tree(T, B=1, theta=(7, 10)):
@@ -182,3 +172,22 @@ def test_theta_one_is_canonical_cover():
                 x += w
             assert recs == greedy
             assert len(recs) <= max(1, 2 * math.ceil(math.log2(te - ts)))
+
+
+# ---- planted mistake: the pins above must catch a slip in the oracle's descent ----------------
+
+def test_pins_catch_a_wrong_completion_test(monkeypatch):
+    # Plant a slip in Algorithm 3's completion test of an intermediate node (tau_v = b + 1,
+    # in block units): compare with b instead.  The stitch-count invariant must fail.
+    from _mutate import mutant
+    import oracle.tree as ot
+    bad = mutant(ot.StreamSegmentTree._insert, "complete and v.tau == b + 1", "complete and v.tau == b")
+    monkeypatch.setattr(ot.StreamSegmentTree, "_insert", bad)
+    t = _tree(0)
+    z = np.zeros((1,))
+    counts_ok = True
+    for T in range(1, 64):
+        before = t.stitch_count
+        t.append(z)
+        counts_ok &= t.stitch_count - before == ((T & -T).bit_length() - 1)
+    assert not counts_ok
