@@ -15,7 +15,10 @@
  *  - Time ranges are half open, 0 <= t_s < t_e <= T.
  *  - Pointers are device pointers unless the call's `io` argument is
  *    TK_IO_HOST, in which case the data pointers are host pointers and the
- *    library copies through its own device staging buffers.
+ *    library copies through its own device staging buffers.  A pointer passed
+ *    as device memory must be device (or managed) memory of the tree's GPU;
+ *    anything else (host memory, another GPU's memory) gives TK_ERR_ARG
+ *    before any work is issued.
  *  - The caller owns every buffer it passes; the library owns the tree's
  *    device arena and workspaces.  Inputs are consumed before the call's
  *    stream work completes; the library never keeps a caller pointer.
@@ -35,7 +38,7 @@
 extern "C" {
 #endif
 
-#define TK_MAX_MODES 6
+#define TK_MAX_MODES 8
 
 typedef enum tk_status {
   TK_OK = 0,
@@ -89,6 +92,10 @@ typedef struct tk_query_info {
   int64_t device_cycles;            /* SM clock cycles the query's job group spent on it */
   int64_t eig_cycles;               /* of which in the eigensolver (Jacobi) */
   int64_t qr_cycles;                /* of which in Householder QR (partial hits and Phi_n) */
+  int64_t hit_cycles;               /* stage 1: hit set, stored or partial-hit decompositions */
+  int64_t init_cycles;              /* stage 2: QR of the stacked factors and the HOSVD start */
+  int64_t als_cycles;               /* stage 3: the ALS iterations of Algorithm 2 */
+  int64_t out_cycles;               /* stage 4: core and factor assembly into the output */
 } tk_query_info;
 
 typedef struct tk_tree tk_tree;
@@ -105,8 +112,9 @@ int tk_config_default(tk_config* cfg);
  * device bytes the tree holds (node arena, workspaces, staging buffers,
  * the open block's slices) above the budget returns TK_ERR_NOMEM before
  * changing anything; so does tk_tree_create when the empty tree does not fit.
- * Not counted: the moment an arena that grows holds its old and new copies
- * together, and a server's own buffers (sized by tk_server_config). */
+ * An arena that grows holds its old and new copies together while the nodes
+ * are copied, and the check counts both.  Not counted: a server's own
+ * buffers (sized by tk_server_config). */
 int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out);
 void tk_tree_destroy(tk_tree* t);
 
@@ -251,30 +259,39 @@ void tk_server_destroy(tk_server* s);
 /* ---- Allocation-free range queries (no counterpart in the paper) --------
  *
  * tk_range_query_batch_noalloc answers the same batched range queries as
- * tk_range_query_batch with io = TK_IO_DEVICE, bit for bit, but makes no
- * device allocation of any kind: no cudaMalloc/cudaFree and no allocating
- * library routine.  It exists for callers that cannot let a library allocate
- * device memory at query time: code that runs under a memory manager or
- * arena of its own (an embedding runtime, a database engine), real-time or
- * serving loops whose latency budget rules out the device-wide
- * synchronization that cudaMalloc/cudaFree may cause, and processes that
- * must keep a fixed device-memory footprint after start-up.
+ * tk_range_query_batch with io = TK_IO_DEVICE, but makes no device
+ * allocation of any kind: no cudaMalloc/cudaFree and no allocating library
+ * routine.  Its answers equal tk_range_query_batch's to rounding (the
+ * regular call runs queries with many hits on wider thread groups, which sums
+ * in another order): within 1e-9 relative error and 1e-3 rad in FP64 and
+ * 1e-6 per element in FP32, as its tests check.
+ *
+ * It exists for callers that cannot let a library allocate device memory at
+ * query time: code that runs under a memory manager or arena of its own (an
+ * embedding runtime, a database engine), real-time or serving loops whose
+ * latency budget rules out the device-wide synchronization that
+ * cudaMalloc/cudaFree may cause, and processes that must keep a fixed
+ * device-memory footprint after start-up.
  *
  * Its scratch is one file-scope device array of TK_NOALLOC_SCRATCH_BYTES
  * (16 MiB), held by every GPU that loads the library until the process
  * exits.  The first call on a device resolves the array's address on that
  * device (set-up, once per device); make that first call before any CUDA
  * stream capture.  All calls share the array and it keeps the last call's
- * contents: the call clears what must start at zero (its status word), and
+ * contents: the call clears what must start at zero (its job counter), and
  * calls whose work overlaps on the GPU (two streams, two trees, two host
- * threads) race on it, so serialize them.
+ * threads) race on it, so serialize them.  Device-side errors (an invalid
+ * range, a job that overflows its workspace) set the tree's own sticky status
+ * word, as for every other call, and tk_sync reports them.
  *
  * ranges (2n int64), offsets (n+1 int64, from tk_batch_layout) and out are
  * device pointers owned by the caller, as for tk_range_query_batch.  info is
  * an optional host array of n reports; with info the call synchronizes and
- * also reports device-side errors, without it the call is asynchronous.
+ * returns what tk_sync would, without it the call is asynchronous.
  * Returns TK_ERR_TOO_BIG when one query's workspace (which grows with the
- * tree's capacity, ranks and dimensions) does not fit the scratch array,
+ * tree's capacity, ranks and dimensions) does not fit the scratch array; the
+ * reports of a call with info are staged in the same array (n times
+ * sizeof(tk_query_info) bytes), so with info they also bound n,
  * TK_ERR_STATE when the open leaf block still awaits its decomposition (any
  * regular query, tk_node_payload, or the append that completes the block
  * decomposes it), and the usual argument and rank errors. */

@@ -13,7 +13,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtucket.so")
-MAX_MODES = 6
+MAX_MODES = 8
 
 TK_F64, TK_F32 = 0, 1
 TK_IO_DEVICE, TK_IO_HOST = 0, 1
@@ -45,7 +45,9 @@ class TkQueryInfo(ctypes.Structure):
     _fields_ = [("ranks", ctypes.c_int32 * MAX_MODES), ("iters", ctypes.c_int32),
                 ("n_hits", ctypes.c_int32), ("fit_err", ctypes.c_double), ("eig_sweeps", ctypes.c_int32),
                 ("eig_max_order", ctypes.c_int32), ("device_cycles", ctypes.c_int64),
-                ("eig_cycles", ctypes.c_int64), ("qr_cycles", ctypes.c_int64)]
+                ("eig_cycles", ctypes.c_int64), ("qr_cycles", ctypes.c_int64),
+                ("hit_cycles", ctypes.c_int64), ("init_cycles", ctypes.c_int64),
+                ("als_cycles", ctypes.c_int64), ("out_cycles", ctypes.c_int64)]
 
 
 class TkServerConfig(ctypes.Structure):
@@ -133,6 +135,22 @@ def _np_dtype(dtype):
     return np.float64 if dtype == "f64" else np.float32
 
 
+def _device_tensor(x, name, device, dtype=None, shape=None):
+    """Check that x is a contiguous CUDA tensor on `device` (torch dtype name
+    `dtype`, e.g. "int64", and shape `shape` where given): the kernels read
+    it directly, so a host buffer or another GPU's would fault."""
+    if not (hasattr(x, "is_cuda") and x.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor on cuda:{device}")
+    if x.device.index != device:
+        raise ValueError(f"{name} is on {x.device}, the tree is on cuda:{device}")
+    if dtype is not None and str(x.dtype) != "torch." + dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, not {x.dtype}")
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(x.shape)}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def _ptr(x):
     """Address of a torch tensor or numpy array (contiguous)."""
     if hasattr(x, "data_ptr"):
@@ -182,6 +200,7 @@ class Tree:
         _check(lib().tk_tree_create(ctypes.byref(cfg), s, ctypes.byref(h)), "tk_tree_create")
         self.h = h
         self.B = int(leaf_slices)
+        self.device = int(device)
 
     def save(self, path):
         """Write the tree to a file (tk_tree_save; synchronous)."""
@@ -206,6 +225,7 @@ class Tree:
         self.dtype = "f64" if cfg.dtype == TK_F64 else "f32"
         self.np_dtype = _np_dtype(self.dtype)
         self.B = int(cfg.leaf_slices)
+        self.device = int(cfg.device)
         return self
 
     def close(self):
@@ -225,6 +245,8 @@ class Tree:
         io = TK_IO_DEVICE if hasattr(X, "is_cuda") and X.is_cuda else TK_IO_HOST
         if io == TK_IO_HOST:
             X = np.ascontiguousarray(X, dtype=self.np_dtype)
+        else:
+            _device_tensor(X, "X", self.device, self._torch_dtype(), (X.shape[0],) + self.dims)
         _check(lib().tk_tree_build(self.h, _ptr(X), int(X.shape[0]), io), "tk_tree_build")
 
     def append(self, X_T):
@@ -232,7 +254,21 @@ class Tree:
         io = TK_IO_DEVICE if hasattr(X_T, "is_cuda") and X_T.is_cuda else TK_IO_HOST
         if io == TK_IO_HOST:
             X_T = np.ascontiguousarray(X_T, dtype=self.np_dtype)
+        else:
+            _device_tensor(X_T, "X_T", self.device, self._torch_dtype(), self.dims)
         _check(lib().tk_stream_append(self.h, _ptr(X_T), io), "tk_stream_append")
+
+    def _torch_dtype(self):
+        return "float64" if self.dtype == "f64" else "float32"
+
+    def _check_batch_args(self, ranges, offsets, out):
+        n = int(ranges.shape[0]) if hasattr(ranges, "shape") and len(ranges.shape) == 2 else -1
+        _device_tensor(ranges, "ranges", self.device, "int64", (max(n, 0), 2))
+        _device_tensor(offsets, "offsets", self.device, "int64", (n + 1,))
+        _device_tensor(out, "out", self.device, self._torch_dtype())
+        if len(out.shape) != 1:
+            raise ValueError("out must be one-dimensional")
+        return n
 
     @property
     def T(self):
@@ -308,8 +344,8 @@ class Tree:
         of offsets[-1] elements of the tree's dtype.  info: optional host
         array of TkQueryInfo (makes the call synchronous).
         """
+        n = self._check_batch_args(ranges, offsets, out)
         rarr, _ = self._ranks_arg(ranks)
-        n = int(ranges.shape[0])
         ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
         _check(lib().tk_range_query_batch(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), ip,
                                           TK_IO_DEVICE), "tk_range_query_batch")
@@ -320,9 +356,10 @@ class Tree:
         Same results as query_batch; the engine's scratch is a fixed 16 MiB
         device array shared by all such calls (serialize overlapping calls).
         """
+        n = self._check_batch_args(ranges, offsets, out)
         rarr, _ = self._ranks_arg(ranks)
         ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
-        _check(lib().tk_range_query_batch_noalloc(self.h, int(ranges.shape[0]), _ptr(ranges), _ptr(offsets),
+        _check(lib().tk_range_query_batch_noalloc(self.h, n, _ptr(ranges), _ptr(offsets),
                                                   rarr, _ptr(out), ip), "tk_range_query_batch_noalloc")
 
     def query_batch_host(self, ranges, offsets=None, out=None, ranks=None, with_info=True):

@@ -67,6 +67,18 @@ namespace {
 
 int cuda_ok(cudaError_t e) { return e == cudaSuccess ? TK_OK : TK_ERR_CUDA; }
 
+// A caller's buffer passed as device memory must be device (or managed)
+// memory of the tree's GPU: a host pointer handed to a kernel would fault.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 int dalloc(DevBuf& b, size_t bytes) {
   if (b.bytes >= bytes && b.ptr) return TK_OK;
   if (b.ptr) cudaFree(b.ptr);
@@ -196,7 +208,10 @@ int ensure_capacity(tk_tree* t, int64_t need_blocks) {
     new_arena += (size_t)L.nslots * t->core_stride * es;
     for (int n = 1; n < p; ++n) new_arena += (size_t)L.nslots * t->fac_stride[n] * es;
     new_arena += (size_t)L.nlevels * Tcap_new * r0 * es + (size_t)L.nslots * TK_MAXP * sizeof(int);
-    if (!within_budget(t, old_arena, new_arena)) return TK_ERR_NOMEM;
+    // the old arena is released only after its levels were copied into the
+    // new one, so both are held at once
+    (void)old_arena;
+    if (!within_budget(t, 0, new_arena)) return TK_ERR_NOMEM;
   }
   DevBuf core, fac[TK_MAXP], tf, nr;
   int rc = dalloc(core, (size_t)L.nslots * t->core_stride * es);
@@ -695,8 +710,9 @@ int tk_sync(tk_tree* t) {
 }
 
 int tk_tree_build(tk_tree* t, const void* X, int64_t T, int io) {
-  if (!t || !X || T < 1) return TK_ERR_ARG;
+  if (!t || !X || T < 1 || (io != TK_IO_DEVICE && io != TK_IO_HOST)) return TK_ERR_ARG;
   if (t->T != 0) return TK_ERR_STATE;
+  if (io == TK_IO_DEVICE && !on_device(X, t->dev)) return TK_ERR_ARG;
   DeviceGuard g(t->dev);
   const int B = t->cfg.leaf_slices;
   const int64_t nb = T / B, nbt = (T + B - 1) / B;
@@ -739,7 +755,8 @@ int tk_tree_build(tk_tree* t, const void* X, int64_t T, int io) {
 }
 
 int tk_stream_append(tk_tree* t, const void* slice, int io) {
-  if (!t || !slice) return TK_ERR_ARG;
+  if (!t || !slice || (io != TK_IO_DEVICE && io != TK_IO_HOST)) return TK_ERR_ARG;
+  if (io == TK_IO_DEVICE && !on_device(slice, t->dev)) return TK_ERR_ARG;
   DeviceGuard g(t->dev);
   const int B = t->cfg.leaf_slices;
   int rc = ensure_capacity(t, (t->T + 1 + B - 1) / B);
@@ -823,7 +840,10 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
                          void* out, tk_query_info* info, int io) {
   if (!t || n < 0) return TK_ERR_ARG;
   if (n == 0) return TK_OK;
-  if (!ranges || !offsets || !out) return TK_ERR_ARG;
+  if (!ranges || !offsets || !out || (io != TK_IO_DEVICE && io != TK_IO_HOST)) return TK_ERR_ARG;
+  if (io == TK_IO_DEVICE &&
+      !(on_device(ranges, t->dev) && on_device(offsets, t->dev) && on_device(out, t->dev)))
+    return TK_ERR_ARG;
   DeviceGuard g(t->dev);
   int rq[TK_MAXP];
   int rc = check_ranks(t, ranks, rq);
@@ -908,7 +928,7 @@ extern "C" {
 
 int tk_range_query(tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks, void* out, tk_query_info* info,
                    int io) {
-  if (!t || !out) return TK_ERR_ARG;
+  if (!t || !out || (io != TK_IO_DEVICE && io != TK_IO_HOST)) return TK_ERR_ARG;
   if (!(t_s >= 0 && t_s < t_e && t_e <= t->T)) return TK_ERR_RANGE;
   int rq[TK_MAXP];
   int rc = check_ranks(t, ranks, rq);
@@ -978,8 +998,9 @@ int tk_node_payload(tk_tree* t, int level, int64_t index, void* out_host, int64_
 
 // ---- Allocation-free batched range queries ---------------------------------
 // The scratch of tk_range_query_batch_noalloc: a fixed device array instead of
-// the tree's allocated workspaces.  Layout per call: [0, 256) status word,
-// then the optional per-query reports, then one workspace chunk per CTA.
+// the tree's allocated workspaces.  Layout per call: [0, 256) the job
+// counter, then the optional per-query reports, then one workspace chunk per
+// CTA.
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TK_NOALLOC_SCRATCH_BYTES];
@@ -1001,6 +1022,8 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
                                             tk_query_info* info) {
   if (!t || n < 1 || !ranges_dev || !offsets_dev || !out_dev) return TK_ERR_ARG;
   if (t->dev < 0 || t->dev >= kMaxDevices) return TK_ERR_ARG;
+  if (!(on_device(ranges_dev, t->dev) && on_device(offsets_dev, t->dev) && on_device(out_dev, t->dev)))
+    return TK_ERR_ARG;
   int rq[TK_MAXP];
   int rc = check_ranks(t, ranks, rq);
   if (rc) return rc;
@@ -1028,15 +1051,16 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
   const int fit = (int)std::min<size_t>((TK_NOALLOC_SCRATCH_BYTES - head) / per_cta_bytes, 1 << 20);
   const int grid = std::max(1, std::min(grid_for(t, n), fit));
   char* base = (char*)d.ptr;
-  rc = cuda_ok(cudaMemsetAsync(base, 0, 256, t->stream));  // status word starts at zero
-  if (rc) return rc;
   TkWorkspace ws{};
   ws.base = base + head;
   ws.per_cta = (int64_t)(per_cta_bytes / t->es);
   ws.nsm = 0;
   ws.smem_arena = (size_t)t->nsm_stitch;
   ws.warps = warps;
-  ws.status = (int*)base;
+  // device-side errors go to the tree's own sticky status word (allocated at
+  // tk_tree_create), so that tk_sync reports them after an asynchronous call;
+  // the job counter (zeroed by the launcher) lives in the scratch array
+  ws.status = (int*)t->status.ptr;
   ws.counter = (unsigned*)(base + 64);
   TkQueryBatch qb{};
   qb.n = n;
@@ -1049,15 +1073,10 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
   t->launches += 1;
   if (rc) return rc;
   if (!info) return TK_OK;
-  int st = 0;
   rc = cuda_ok(cudaMemcpyAsync(info, base + 256, sizeof(tk_query_info) * (size_t)n, cudaMemcpyDeviceToHost,
                                t->stream));
-  if (rc == TK_OK) rc = cuda_ok(cudaMemcpyAsync(&st, base, sizeof(int), cudaMemcpyDeviceToHost, t->stream));
-  if (rc == TK_OK) rc = cuda_ok(cudaStreamSynchronize(t->stream));
   if (rc) return rc;
-  if (st == TK_DEV_ERR_RANGE) return TK_ERR_RANGE;
-  if (st != 0) return TK_ERR_WORKSPACE;
-  return TK_OK;
+  return tk_sync(t);
 }
 
 // ---- Tree files --------------------------------------------------------------

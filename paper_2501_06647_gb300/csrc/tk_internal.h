@@ -9,7 +9,7 @@
 #define TK_MAXL 40      // tree levels (2^39 leaf blocks)
 #define TK_MAXH 64      // hits per stitch job handled by the kernel
 #define TK_NT 256       // threads per CTA of the leaf kernel
-#define TK_HITREC_BYTES 160  // bytes of one hit record in a stitch job's workspace
+#define TK_HITREC_BYTES 176  // bytes of one hit record in a stitch job's workspace
 
 // Device view of a tree: dimensions, the implicit dyadic node numbering and
 // the pooled HBM arena.  Passed by value to every kernel.

@@ -526,6 +526,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     return (lim - reinterpret_cast<const char*>(cx.A)) >= (int64_t)(nel * sizeof(S)) ? cx.A : nullptr;
   };
 
+  const long long t_hits = clock64();
   // ---- non-temporal bases Phi_n = Q_n R_n, and the implicit HOSVD start ---
   for (int n = 1; n < p; ++n) {
     const int Dn = tv.D[n], kn = cx.k[n], cn = cx.c[n];
@@ -567,6 +568,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     eig(n, cn, cx.E[n], cx.ro[n]);
   }
 
+  const long long t_init = clock64();
   // ---- Algorithm 2 iterations --------------------------------------------
   S e_prev = S(-1);
   S e = 0;
@@ -644,6 +646,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     e_prev = e;
   }
   if (it > maxit) it = maxit;
+  const long long t_als = clock64();
 
   // ---- outputs: core, U^(1) = blockdiag(V~_i^(1)) C, U^(n) = Q_n E_n --------
   {
@@ -730,6 +733,10 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       info->device_cycles = (int64_t)(clock64() - t_start);
       info->eig_cycles = (int64_t)eig_cyc;
       info->qr_cycles = (int64_t)qr_cyc;
+      info->hit_cycles = (int64_t)(t_hits - t_start);
+      info->init_cycles = (int64_t)(t_init - t_hits);
+      info->als_cycles = (int64_t)(t_als - t_init);
+      info->out_cycles = (int64_t)(clock64() - t_als);
     }
   }
   G::sync();

@@ -116,3 +116,52 @@ def test_noalloc_refuses_an_undecomposed_open_block():
     t.query_batch_noalloc(r, o, out)
     t.sync()
     t.close()
+
+
+def test_noalloc_device_errors_reach_tk_sync():
+    # An invalid range inside a device-resident batch is found by the kernel; the
+    # asynchronous call (no report) leaves it in the tree's sticky status word,
+    # which the next tk_sync returns.
+    import paper_2501_06647_gb300 as tk
+    dims, ranks = (9, 7), (3, 3, 3)
+    X = series(32, dims, ranks, 16, 0.05, 5)
+    t = engine_tree(X, dims, ranks, 4, 3, 0.0, "f64")
+    dev = torch.device("cuda", 0)
+    Q = np.array([[0, 8], [4, 40]], dtype=np.int64)          # the second ends beyond T = 32
+    offs = t.layout(Q)
+    r, o = torch.from_numpy(Q).to(dev), torch.from_numpy(offs).to(dev)
+    out = torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev)
+    t.query_batch_noalloc(r, o, out)
+    with pytest.raises(tk.TuckerError) as ei:
+        t.sync()
+    assert ei.value.code == -2
+    t.close()
+
+
+def test_noalloc_reports_share_the_scratch_array():
+    # With reports, n tk_query_info records are staged in the 16 MiB array too:
+    # a batch whose reports alone exceed it is refused (TK_ERR_TOO_BIG); the
+    # same batch without reports runs.
+    import paper_2501_06647_gb300 as tk
+    dims, ranks = (9, 7), (3, 3, 3)
+    X = series(32, dims, ranks, 16, 0.05, 6)
+    t = engine_tree(X, dims, ranks, 4, 2, 0.0, "f64")
+    n = (16 << 20) // ctypes.sizeof(tk.TkQueryInfo) + 1
+    dev = torch.device("cuda", 0)
+    Q = np.tile(np.array([[3, 5]], dtype=np.int64), (n, 1))
+    offs = t.layout(Q)
+    r, o = torch.from_numpy(Q).to(dev), torch.from_numpy(offs).to(dev)
+    out = torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev)
+    info = (tk.TkQueryInfo * n)()
+    with pytest.raises(tk.TuckerError) as ei:
+        t.query_batch_noalloc(r, o, out, info=info)
+    assert ei.value.code == -8
+    t.query_batch_noalloc(r, o, out)
+    t.sync()
+    ref_out = torch.zeros(int(offs[1]), dtype=torch.float64, device=dev)
+    t.query_batch(r[:1].contiguous(), o[:2].contiguous(), ref_out)
+    got = out.cpu().numpy()
+    first = ref_out.cpu().numpy()
+    assert np.allclose(got[: int(offs[1])], first, rtol=0, atol=1e-12)
+    assert np.allclose(got[int(offs[-2]):], first, rtol=0, atol=1e-12)
+    t.close()
