@@ -634,13 +634,17 @@ constexpr int kTrdMaxRank = 62;
 // warps in the group.
 __host__ __device__ inline int trd_scratch_elems(int n, int r, int nw) {
   const int wv = nw < r ? nw : r;
-  return 6 * n + 2 * r + 8 + 6 * n * (wv > 0 ? wv : 1);
+  return 6 * n + 2 * r + 8 + r * n + 6 * n * (wv > 0 ? wv : 1);
 }
 
 // The r leading eigenpairs of a symmetric n x n matrix A (lda), r <= n,
 // r <= kTrdMaxRank, executed by group G:
-//   1. Householder tridiagonalization A = Q T Q^T (Golub & Van Loan,
-//      Algorithm 8.3.1), accumulating Q^T in Qt (n x n);
+//   1. Householder tridiagonalization Q^T A Q = T (Golub & Van Loan,
+//      Algorithm 8.3.1).  Q = H_0 H_1 ... H_{n-3} is not formed: reflector
+//      H_k = I - beta_k v_k v_k^T (v_k zero above row k+1, v_k[k+1] = 1) is
+//      kept in row k of A, which the trailing update no longer touches, so
+//      that A is the only n x n array (it fits shared memory up to order
+//      ~220 in FP32);
 //   2. the r largest eigenvalues of T by bisection on Sturm sequence sign
 //      counts (Golub & Van Loan, Section 8.4.1), one warp per eigenvalue and
 //      32 trial points per step (multisection: each step shrinks the
@@ -651,26 +655,28 @@ __host__ __device__ inline int trd_scratch_elems(int n, int r, int nw) {
 //      1e-3 ||T|| form a cluster, whose vectors one warp computes in order,
 //      orthogonalizing every iterate against the cluster's earlier ones;
 //   4. E = Q X (n x r, leading dimension lde), columns in descending order
-//      of the eigenvalues.
-// A is destroyed (its storage then holds X).  vec: trd_scratch_elems(n, r,
-// G::nwarps()) elements; sc: >= 4 elements; cl: >= 64 ints, all private to
-// the group.  Every step has a fixed order, so results are reproducible.
+//      of the eigenvalues: each warp applies H_{n-3}, ..., H_0 to its own
+//      columns of X, with no group barrier between reflectors.
+// The trailing matrix-vector product reads A by columns (A is symmetric):
+// consecutive threads read consecutive addresses.  A is destroyed.  vec:
+// trd_scratch_elems(n, r, G::nwarps()) elements; sc: >= 4 elements; cl: >= 64
+// ints, all private to the group.  Every step has a fixed order, so results
+// are reproducible.
 template <class G, class S>
-__device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* vec, S* sc, int* cl) {
+__device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* sc, int* cl) {
   const int tid = G::rank(), nt = G::size(), lane = tid & 31, warp = tid >> 5, nw = G::nwarps();
   S* d = vec;
   S* e = d + n;
   S* e2 = e + n;
   S* v = e2 + n;
   S* pv = v + n;
-  S* sv = pv + n;
-  S* lam = sv + n;
-  S* wsc = lam + 2 * r + 8;
-  // ---- Householder tridiagonalization, Q accumulated as Qt = Q^T --------
-  for (int idx = tid; idx < n * n; idx += nt) Qt[idx] = (idx / n == idx % n) ? S(1) : S(0);
-  G::sync();
+  S* bet = pv + n;
+  S* lam = bet + n;
+  S* X = lam + 2 * r + 8;  // r x n, row j = eigenvector j of T
+  S* wsc = X + r * n;
+  // ---- Householder tridiagonalization ------------------------------------
   for (int k = 0; k + 2 < n; ++k) {
-    const int m0 = k + 1;
+    const int m0 = k + 1, len = n - m0;
     if (warp == 0) {
       S sig = 0;
       for (int i = m0 + 1 + lane; i < n; i += 32) {
@@ -685,10 +691,15 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
         v1 = alpha <= S(0) ? alpha - mu : -sig / (alpha + mu);
         beta = S(2) * v1 * v1 / (sig + v1 * v1);
         const S inv = S(1) / v1;
-        for (int i = m0 + lane; i < n; i += 32) v[i] = (i == m0) ? S(1) : A[i * lda + k] * inv;
+        for (int i = m0 + lane; i < n; i += 32) {
+          const S vi = (i == m0) ? S(1) : A[i * lda + k] * inv;
+          v[i] = vi;
+          A[k * lda + i] = vi;  // row k is retired: it keeps the reflector
+        }
       }
       if (lane == 0) {
         sc[0] = beta;
+        bet[k] = beta;
         e[k] = mu;
         d[k] = A[k * lda + k];
       }
@@ -696,33 +707,56 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
     G::sync();
     const S beta = sc[0];
     if (beta == S(0)) continue;
-    // p = beta A v (A symmetric: thread i walks column i) and s = beta Q v
-    // (Q^T stored: thread i walks column i of Qt), by the two halves of the group
+    // p = beta A' v on the trailing block A' (rows and columns >= m0); with
+    // more threads than rows, `sp` threads share a row and combine in pv
     {
-      const int half = nt >> 1;
-      const bool second = tid >= half;
-      const int t0 = second ? tid - half : tid;
-      const S* M = second ? Qt : A;
-      const int ldm = second ? n : lda;
-      S* outv = second ? sv : pv;
-      for (int i = (second ? 0 : m0) + t0; i < n; i += half) {
-        S acc = 0;
-        for (int j = m0; j < n; ++j) acc += M[j * ldm + i] * v[j];
-        outv[i] = beta * acc;
+      int sp = nt / len;
+      sp = sp > 4 ? 4 : sp;
+      if (sp < 2) {
+        for (int i = m0 + tid; i < n; i += nt) {
+          S acc = 0;
+          for (int j = m0; j < n; ++j) acc += A[j * lda + i] * v[j];
+          pv[i] = beta * acc;
+        }
+      } else {
+        const int t = tid % len, part = tid / len;
+        if (part < sp) {
+          const int i = m0 + t;
+          const int j0 = m0 + (len * part) / sp, j1 = m0 + (len * (part + 1)) / sp;
+          S acc = 0;
+          for (int j = j0; j < j1; ++j) acc += A[j * lda + i] * v[j];
+          wsc[part * n + i] = acc;
+        }
+        G::sync();
+        for (int i = m0 + tid; i < n; i += nt) {
+          S acc = 0;
+          for (int q = 0; q < sp; ++q) acc += wsc[q * n + i];
+          pv[i] = beta * acc;
+        }
       }
     }
     G::sync();
+    // K = beta/2 p^T v (every warp reduces it itself), w = p - K v, and the
+    // rank-2 update A' -= v w^T + w v^T, consecutive threads on a row
     S kk = 0;
     for (int i = m0 + lane; i < n; i += 32) kk += pv[i] * v[i];
     kk = warp_sum(kk) * (beta * S(0.5));
-    // A <- A - v w^T - w v^T with w = p - K v; Q <- Q - s v^T (rows by warps)
-    for (int i = m0 + warp; i < n; i += nw) {
-      const S vi = v[i], wi = pv[i] - kk * vi;
-      for (int j = m0 + lane; j < n; j += 32) A[i * lda + j] -= vi * (pv[j] - kk * v[j]) + wi * v[j];
-    }
-    for (int j = m0 + warp; j < n; j += nw) {
-      const S vj = v[j];
-      for (int i = lane; i < n; i += 32) Qt[j * n + i] -= vj * sv[i];
+    {
+      const int tot = len * len;
+      const int di = nt / len, dj = nt - di * len;
+      int i = tid / len, j = tid - (tid / len) * len;
+      for (int idx = tid; idx < tot; idx += nt) {
+        const int gi = m0 + i, gj = m0 + j;
+        const S vi = v[gi], vj = v[gj];
+        const S wi = pv[gi] - kk * vi, wj = pv[gj] - kk * vj;
+        A[gi * lda + gj] -= vi * wj + wi * vj;
+        j += dj;
+        i += di;
+        if (j >= len) {
+          j -= len;
+          ++i;
+        }
+      }
     }
     G::sync();
   }
@@ -793,7 +827,6 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
   G::sync();
   const int nclus = cl[63];
   const int nwv = nw < r ? nw : r;
-  S* X = A;  // r x n, row j = eigenvector of T for lam[j]
   if (warp < nwv) {
     S* xw = wsc + warp * 6 * n;
     S* ua = xw + n;   // reciprocals of U's diagonal
@@ -877,12 +910,40 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* Qt, S* E, int lde, S* ve
     }
   }
   G::sync();
-  // ---- back-transformation E = Q X^T (n x r) ------------------------------
-  for (int idx = tid; idx < n * r; idx += nt) {
-    const int i = idx / r, j = idx % r;
-    S acc = 0;
-    for (int k = 0; k < n; ++k) acc += Qt[k * n + i] * X[j * n + k];
-    E[i * lde + j] = acc;
+  // ---- back-transformation E = Q X^T: each warp applies H_{n-3} .. H_0 to
+  // its own vectors (up to 4 at a time, held in its scratch) ---------------
+  const int vpw = (r + nw - 1) / nw < 4 ? (r + nw - 1) / nw : 4;
+  for (int j0 = warp * vpw; j0 < r; j0 += nw * vpw) {
+    const int nv = (r - j0) < vpw ? (r - j0) : vpw;
+    S* y = wsc + warp * 6 * n;  // nv contiguous vectors of n
+    for (int c = 0; c < nv; ++c)
+      for (int i = lane; i < n; i += 32) y[c * n + i] = X[(j0 + c) * n + i];
+    __syncwarp();
+    for (int k = n - 3; k >= 0; --k) {
+      const S beta = bet[k];
+      if (beta == S(0)) continue;
+      const int m0 = k + 1;
+      const S* vk = A + k * lda;  // v_k[m0..n), v_k[m0] = 1
+      S dot[4] = {S(0), S(0), S(0), S(0)};
+      for (int i = m0 + lane; i < n; i += 32) {
+        const S vi = vk[i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < nv) dot[c] += vi * y[c * n + i];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dot[c] = warp_sum(dot[c]) * beta;
+      for (int i = m0 + lane; i < n; i += 32) {
+        const S vi = vk[i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < nv) y[c * n + i] -= dot[c] * vi;
+      }
+      __syncwarp();
+    }
+    for (int c = 0; c < nv; ++c)
+      for (int i = lane; i < n; i += 32) E[i * lde + j0 + c] = y[c * n + i];
+    __syncwarp();
   }
   G::sync();
 }

@@ -3,6 +3,7 @@
 // build (Section 4.2), stream update (Algorithms 3-4) and range query
 // (Section 6.1).
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -56,7 +57,7 @@ struct tk_tree {
   DevBuf ws_stitch, ws_leaf, status;
   int64_t ws_stitch_per_cta = 0, ws_leaf_per_cta = 0;
   int ws_stitch_ctas = 0, ws_leaf_ctas = 0;
-  int nsm_stitch = 0, nsm_leaf = 0;
+  int nsm_stitch = 0, nsa_leaf = 0, nsv_leaf = 0;
   int sm_count = 0;
   // staging for host io and batch metadata
   DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
@@ -317,7 +318,8 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
 
 // Workspace of one leaf cluster (see TkLeafLayout), with every rank at its
 // build value and the block at its full B slices: bounds for any block.
-TkLeafLayout leaf_layout(const tk_tree* t, int nsm, int64_t* per_cluster) {
+// nsa / nsv: the shared-memory capacities (orders) of the eigensolvers.
+TkLeafLayout leaf_layout(const tk_tree* t, int nsa, int nsv, int64_t* per_cluster) {
   TkLeafLayout ly{};
   const int p = t->p;
   const int CL = TK_LEAF_CL;
@@ -369,14 +371,14 @@ TkLeafLayout leaf_layout(const tk_tree* t, int nsm, int64_t* per_cluster) {
     for (int n = 0; n < p; ++n) rmx = std::max<int>(rmx, (int)r[n]);
     ly.trd = take(tk::trd_scratch_elems((int)neig, rmx, TK_NT / 32));
   }
-  ly.nsm = nsm;
+  ly.nsa = nsa;
+  ly.nsv = nsv;
   ly.neig = (int)neig;
   ly.rmax = 1;
   for (int n = 0; n < p; ++n) ly.rmax = std::max<int>(ly.rmax, (int)r[n]);
   ly.half = neig / 2 + 2;
-  ly.eig_in_smem = neig <= nsm;
-  if (!ly.eig_in_smem) {
-    ly.nsm = 0;  // the eigensolver works in the CTA's global region: no shared arrays
+  if (neig > nsv) {
+    // some eigenproblem may not fit shared memory: it works in the CTA's global region
     ly.A = take(neig * neig);
     ly.V = take(neig * neig);
     ly.w = take(neig + 2);
@@ -404,11 +406,22 @@ int pick_nsm_stitch(const tk_tree* t) {
 
 int stitch_warps(const tk_tree* t) { (void)t; return 8; }
 
-int pick_nsm_leaf(const tk_tree* t) {
-  int need = t->cfg.leaf_slices;
+// Shared-memory capacities of the leaf kernel's eigensolvers: the Jacobi
+// arrays for orders below the tridiagonal method's, and A (the only n x n
+// array of the tridiagonal method) for the largest order that fits next to
+// the contraction buffers in a CTA's shared memory.
+void pick_nsm_leaf(const tk_tree* t, int* nsa, int* nsv) {
+  int need = t->cfg.leaf_slices, rmax = 1;
   for (int n = 1; n < t->p; ++n) need = std::max<int>(need, (int)t->cfg.dims[n]);
-  const int cap = t->es == 8 ? 100 : 150;
-  return std::max(2, std::min(need, cap));
+  for (int n = 0; n < t->p; ++n) rmax = std::max<int>(rmax, t->cfg.ranks[n]);
+  rmax = std::min(rmax, need);
+  *nsv = std::max(2, std::min(need, tk::kTrdMinOrder - 1));
+  const size_t limit = 227 * 1024 - 512;
+  const size_t base = tk_leaf_smem_bytes(t->cfg.dtype, 0, *nsv, need, rmax);
+  int a = 0;
+  if (base < limit) a = (int)std::sqrt((double)(limit - base - 16) / (double)t->es);
+  *nsa = std::max(*nsv, std::min(need, a));
+  while (*nsa > *nsv && tk_leaf_smem_bytes(t->cfg.dtype, *nsa, *nsv, need, rmax) > limit) --*nsa;
 }
 
 // Stitch workspace: one chunk per CTA of the grid.
@@ -429,9 +442,9 @@ int ensure_ws_stitch(tk_tree* t, int want_ctas) {
 
 // Leaf workspace: one chunk per cluster of the grid.
 int ensure_ws_leaf(tk_tree* t, int want_clusters, TkLeafLayout* ly) {
-  if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
+  if (t->nsa_leaf == 0) pick_nsm_leaf(t, &t->nsa_leaf, &t->nsv_leaf);
   int64_t per = 0;
-  *ly = leaf_layout(t, t->nsm_leaf, &per);
+  *ly = leaf_layout(t, t->nsa_leaf, t->nsv_leaf, &per);
   int n = std::max(1, want_clusters);
   if (per != t->ws_leaf_per_cta || n > t->ws_leaf_ctas) {
     n = std::max(n, t->ws_leaf_ctas);
@@ -481,10 +494,11 @@ int grid_for(tk_tree* t, int njobs) {
 // elements), each of `ell` slices: one cluster per block, persistent.
 int run_leaves(tk_tree* t, const void* raw, int64_t block_stride, int64_t first, int njobs, int ell) {
   if (njobs <= 0) return TK_OK;
-  if (t->nsm_leaf == 0) t->nsm_leaf = pick_nsm_leaf(t);
+  if (t->nsa_leaf == 0) pick_nsm_leaf(t, &t->nsa_leaf, &t->nsv_leaf);
   int64_t per = 0;
-  const TkLeafLayout probe = leaf_layout(t, t->nsm_leaf, &per);
-  int maxc = tk_leaf_max_clusters(t->cfg.dtype, tk_leaf_smem_bytes(t->cfg.dtype, probe.nsm, probe.neig, probe.rmax));
+  const TkLeafLayout probe = leaf_layout(t, t->nsa_leaf, t->nsv_leaf, &per);
+  int maxc = tk_leaf_max_clusters(t->cfg.dtype,
+                                  tk_leaf_smem_bytes(t->cfg.dtype, probe.nsa, probe.nsv, probe.neig, probe.rmax));
   if (maxc < 1) maxc = 1;
   const int ncl = std::min(njobs, maxc);
   TkLeafLayout ly{};

@@ -87,10 +87,10 @@ struct TkLeafLayout {
   int64_t trd;             // vectors of the tridiagonal eigensolver
   int64_t A, V, w, cs, pq; // eigensolver arrays when they do not fit shared memory
   int64_t half;            // entries of each rotation array (order / 2 + 2)
-  int nsm;                 // largest eig order kept in shared memory
+  int nsa;                 // largest order whose eigenproblem matrix A is in shared memory
+  int nsv;                 // largest order whose Jacobi arrays (V, rotations) are in shared memory
   int neig;                // largest Gram order of a block
   int rmax;                // largest rank
-  int eig_in_smem;
 };
 
 // Launchers (tk_kernels.cu, tk_leaf.cu).  All asynchronous on `stream`.
@@ -98,7 +98,7 @@ struct TkLeafLayout {
 int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t block_stride,
                    int64_t first_block, int njobs, int ell, const TkWorkspace& ws,
                    const TkLeafLayout& ly, int nclusters, cudaStream_t stream);
-size_t tk_leaf_smem_bytes(int dtype, int nsm, int neig, int rmax);
+size_t tk_leaf_smem_bytes(int dtype, int nsa, int nsv, int neig, int rmax);
 int tk_leaf_max_clusters(int dtype, size_t smem);
 int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int njobs,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);

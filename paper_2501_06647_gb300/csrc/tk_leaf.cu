@@ -380,19 +380,22 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
   LeafSm<S>& sm = *reinterpret_cast<LeafSm<S>*>(smem_raw);
   const int crank = (int)cluster_rank();
   const int cid = (int)cluster_id(), ncl = (int)num_clusters();
-  const int nsm = ly.nsm;
-  const int half_cap = nsm / 2 + 2;
+  // shared memory: the header, the Jacobi arrays for orders <= nsv, A for
+  // orders <= nsa (the tridiagonal method needs A only; Jacobi also V),
+  // then the contraction buffers
+  const int nsa = ly.nsa, nsv = ly.nsv;
+  const int half_cap = nsv / 2 + 2;
   size_t off = kHdr;
   int* js_pq = reinterpret_cast<int*>(smem_raw + off);
   off += align16(half_cap * sizeof(int));
   S* js_c = reinterpret_cast<S*>(smem_raw + off);
   S* js_s = js_c + half_cap;
   S* js_w = js_s + half_cap;
-  off += align16(sizeof(S) * (2 * half_cap + nsm + 2));
+  off += align16(sizeof(S) * (2 * half_cap + nsv + 2));
   S* sA = reinterpret_cast<S*>(smem_raw + off);
-  off += align16(sizeof(S) * (size_t)nsm * nsm);
+  off += align16(sizeof(S) * (size_t)nsa * nsa);
   S* sV = reinterpret_cast<S*>(smem_raw + off);
-  off += align16(sizeof(S) * (size_t)nsm * nsm);
+  off += align16(sizeof(S) * (size_t)nsv * nsv);
   S* tile = reinterpret_cast<S*>(smem_raw + off);
   off += align16(sizeof(S) * (size_t)kKC * (((ly.neig + 3) & ~3) + 4));
   S* stage = reinterpret_cast<S*>(smem_raw + off);
@@ -401,18 +404,24 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
 
   S* wc = reinterpret_cast<S*>(wsd.base) + (int64_t)cid * wsd.per_cta;  // the cluster's chunk
   S* wt = wc + ly.cta + (int64_t)crank * ly.cta_stride;                 // this CTA's part
-  const bool eig_smem = ly.eig_in_smem != 0;
-  S* A = eig_smem ? sA : wt + ly.A;
-  S* V = eig_smem ? sV : wt + ly.V;
-  S* ew = eig_smem ? js_w : wt + ly.w;
-  JacobiScratch<S> js;
-  js.pq = eig_smem ? js_pq : reinterpret_cast<int*>(wt + ly.pq);
-  js.c = eig_smem ? js_c : wt + ly.cs;
-  js.s = eig_smem ? js_s : wt + ly.cs + ly.half;
-  js.flag = &sm.flag;
-  js.red = sm.red;
-  js.nsw = &sm.nsw;
-  js.thr = &sm.thr;
+  // eigenproblem buffers for order dn: shared memory when they fit, else
+  // this CTA's global region (ly.A etc. exist whenever some order exceeds nsv)
+  auto uses_trd = [&](int dn, int rk) { return dn >= kTrdMinOrder && rk <= kTrdMaxRank; };
+  auto eig_A = [&](int dn, int rk) -> S* { return (uses_trd(dn, rk) ? dn <= nsa : dn <= nsv) ? sA : wt + ly.A; };
+  auto jac = [&](int dn, S** V, S** w) -> JacobiScratch<S> {
+    const bool sm_ok = dn <= nsv;
+    JacobiScratch<S> js;
+    js.pq = sm_ok ? js_pq : reinterpret_cast<int*>(wt + ly.pq);
+    js.c = sm_ok ? js_c : wt + ly.cs;
+    js.s = sm_ok ? js_s : wt + ly.cs + ly.half;
+    js.flag = &sm.flag;
+    js.red = sm.red;
+    js.nsw = &sm.nsw;
+    js.thr = &sm.thr;
+    *V = sm_ok ? sV : wt + ly.V;
+    *w = sm_ok ? js_w : wt + ly.w;
+    return js;
+  };
   S* T = wt + ly.T;
   const S* U[TK_MAXP];
   for (int n = 0; n < TK_MAXP; ++n) U[n] = wc + ly.U[n];
@@ -464,15 +473,18 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
       const int D = xd[n];
       const int DD = D * D;
       const S* part = wc + ly.part[n];
+      S* A = eig_A(D, rl[n]);
       for (int i = tid; i < DD; i += nt) {
         S a = 0;
         for (int c = 0; c < TK_LEAF_CL; ++c) a += part[(int64_t)c * DD + i];
         A[i] = a;
       }
       __syncthreads();
-      if (D >= kTrdMinOrder && rl[n] <= kTrdMaxRank) {
-        trd_eig<BG, S>(D, rl[n], A, D, V, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
+      if (uses_trd(D, rl[n])) {
+        trd_eig<BG, S>(D, rl[n], A, D, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
       } else {
+        S *V, *ew;
+        JacobiScratch<S> js = jac(D, &V, &ew);
         jacobi_eig<BG, S>(D, rl[n], A, V, T, false, ew, js, maxsw);
         select_top<BG, S>(D, ew, V, rl[n], wc + ly.U[n], rl[n]);
         for (int i = tid; i < DD; i += nt) wc[ly.Vs[n] + i] = V[i];
@@ -502,12 +514,15 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
         cluster_barrier();
         if (crank == 0) {
           const S* Y = wc + ly.Y;
+          S* A = eig_A(dn, rl[n]);
           gram_cols<S>(Y, dn, Rn, 0, Rn, A, dn, tile);
-          if (dn >= kTrdMinOrder && rl[n] <= kTrdMaxRank) {
-            trd_eig<BG, S>(dn, rl[n], A, dn, V, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
+          if (uses_trd(dn, rl[n])) {
+            trd_eig<BG, S>(dn, rl[n], A, dn, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
           } else {
             // Jacobi, warm-started from the mode's previous basis (the HOSVD
             // start's for n >= 2 in the first iteration)
+            S *V, *ew;
+            JacobiScratch<S> js = jac(dn, &V, &ew);
             const bool warm = n > 0 || it > 1;
             if (warm) {
               for (int i = tid; i < dn * dn; i += nt) V[i] = wc[ly.Vs[n] + i];
@@ -577,12 +592,12 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
 
 using namespace tk;
 
-size_t tk_leaf_smem_bytes(int dtype, int nsm, int neig, int rmax) {
+size_t tk_leaf_smem_bytes(int dtype, int nsa, int nsv, int neig, int rmax) {
   const size_t es = dtype == TK_F64 ? 8 : 4;
-  const int half_cap = nsm / 2 + 2;
+  const int half_cap = nsv / 2 + 2;
   size_t b = kHdr + align16(half_cap * sizeof(int));
-  b += align16(es * (2 * half_cap + nsm + 2));
-  b += 2 * align16(es * (size_t)nsm * nsm);
+  b += align16(es * (2 * half_cap + nsv + 2));
+  b += align16(es * (size_t)nsa * nsa) + align16(es * (size_t)nsv * nsv);
   b += align16(es * (size_t)kKC * (((neig + 3) & ~3) + 4));
   b += align16(es * (size_t)kStage);
   b += es * (size_t)neig * ((rmax + 3) & ~3);
@@ -610,7 +625,7 @@ int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t blo
                    int njobs, int ell, const TkWorkspace& ws, const TkLeafLayout& ly, int nclusters,
                    cudaStream_t stream) {
   if (njobs <= 0) return TK_OK;
-  const size_t smem = tk_leaf_smem_bytes(dtype, ly.nsm, ly.neig, ly.rmax);
+  const size_t smem = tk_leaf_smem_bytes(dtype, ly.nsa, ly.nsv, ly.neig, ly.rmax);
   const dim3 grid(TK_LEAF_CL * nclusters);
   if (dtype == TK_F64) {
     if (cudaFuncSetAttribute(leaf_fn<double>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -319,18 +319,19 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     for (int n = 1; n < p; ++n)
       if (cx.c[n] > neig) neig = cx.c[n];
     cx.neig = neig;
-    cx.A = take((int64_t)neig * neig);
-    cx.V = take((int64_t)neig * neig);
-    cx.w = take(neig + 2);
-    cx.cs = take(2 * (neig / 2 + 2));
-    cx.pq = reinterpret_cast<int*>(take_bytes(sizeof(int) * (size_t)(neig / 2 + 2)));
-    // the Jacobi method's warm-start product and saved bases exist only for the
-    // modes whose order is below the tridiagonal method's
+    // the Jacobi method's eigenvector matrix, warm-start product and saved
+    // bases exist only for the modes whose order is below the tridiagonal
+    // method's (which keeps its reflectors in A)
     int njac = 0;
     for (int n = 0; n < p; ++n) {
       const bool trd = cx.c[n] >= kTrdMinOrder && cx.ro[n] <= kTrdMaxRank;
       if (!trd && cx.c[n] > njac) njac = cx.c[n];
     }
+    cx.A = take((int64_t)neig * neig);
+    cx.V = njac > 0 ? take((int64_t)njac * njac) : nullptr;
+    cx.w = take(neig + 2);
+    cx.cs = take(2 * (neig / 2 + 2));
+    cx.pq = reinterpret_cast<int*>(take_bytes(sizeof(int) * (size_t)(neig / 2 + 2)));
     cx.T = njac > 0 ? take((int64_t)njac * njac) : nullptr;
     {
       int rmx = 1;
@@ -430,7 +431,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     const long long c0 = clock64();
     const int rkeep = cx.ro[mode_n];
     if (nsz >= kTrdMinOrder && rkeep <= kTrdMaxRank) {
-      trd_eig<G, S>(nsz, rkeep, A, nsz, V, Edst, lde, cx.trdv, sm.sc, sm.cl);
+      trd_eig<G, S>(nsz, rkeep, A, nsz, Edst, lde, cx.trdv, sm.sc, sm.cl);
     } else {
       S* Vs = cx.Vs[mode_n];
       const bool warm = have_v[mode_n];
