@@ -1,16 +1,23 @@
 #!/usr/bin/env python3
-"""Range-query throughput of the GPU engine on the FP32 plain workload.
+"""Range-query throughput of the GPU engine on the batched rank-16 workload.
 
-One step = one batched launch answering the workload's 1000 range queries
-(Recall, partial-hit QR, Stitch/HOOI, factor assembly: every row of the hot
-path) over a tree already resident in HBM.  Prints ONE JSON line (rank 0).
+One step = one batched launch sequence answering the workload's 10,000
+concurrent range queries (Recall, partial-hit QR, Stitch/HOOI in coefficient
+space, factor assembly: every row of the hot path) over a tree already
+resident in HBM: 200x150 slices, T = 8192, ranks (16,16,16), leaf 16, FP32.
+Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the literal restatement of the
-paper's algorithms) on the host cores instead, on bounded samples of the same
+The line also carries the one-query-per-launch (plain) method on the same
+tree, in-batch p50/p99 latency, the end-to-end number through host buffers,
+rooflines, the FP64 oracle on the host cores (cpu_baseline) and the
+matched-error check, and sections for the FP32 plain workload (100x100,
+rank 10), stream appends, serving and the leaf kernel.  --impl reference
+times the FP64 CPU oracle (the literal restatement of the paper's
+algorithms) on the host cores instead, on bounded samples of the same
 workload.  Multi-GPU runs are replicas (every rank holds the tree and answers
-its own copy of the query batch; no collective on the data path).
+its own copy of the batch; no collective on the data path).
 """
 import argparse
 import ctypes
@@ -31,18 +38,30 @@ import synth  # noqa: E402
 
 METRIC = "range queries/sec + p50/p99 query latency at matched recon error vs plain"
 UNIT = "queries/s"
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes of one batch of the FP32 plain workload (the k_batch launch),
-# from one ncu capture of the current kernel; None until measured, and to be
-# re-measured whenever the kernel changes.
-STITCH_BATCH_DRAM_BYTES = 40.38e6  # 8.76 MB read + 31.62 MB written
+FP32_LANES_PER_SM = 128   # FP32 FMA units per SM (Blackwell)
+# DRAM bytes (read + write) of one k_batch launch answering the 10,000-query
+# batch, from one ncu capture of the current kernel (None: not yet captured
+# for this kernel version).
+BATCH_DRAM_BYTES = None
+ORACLE_T = 1024           # the CPU oracle's tree covers the first 1024 slices
 
 
-def workload_desc(w):
-    return (f"fp32_plain: {w['dims'][0]}x{w['dims'][1]}xT={w['T']} piecewise Tucker rank-{tuple(w['ranks'])}, "
-            f"regime {w['regime']}, sigma {w['sigma']}, leaf {w['B']} slices, {w['n_queries']} log-uniform "
-            f"queries L in [{w['lo']},{w['hi']}], theta 0.7, max_iter 20, tol 0.01")
+def workload_desc(w, name):
+    return (f"{name}: {w['dims'][0]}x{w['dims'][1]}xT={w['T']} piecewise Tucker rank-{tuple(w['ranks'])}, "
+            f"regime {w['regime']}, sigma {w['sigma']}, leaf {w['B']} slices, {w['n_queries']} concurrent "
+            f"log-uniform queries L in [{w['lo']},{w['hi']}], theta 0.7, max_iter 20, tol 0.01, FP32")
+
+
+def series_of(name, T=None):
+    """The workload's seeded series (its first T slices: the generator draws
+    regime by regime, so a prefix is the same for any length)."""
+    w = synth.WORKLOADS[name]
+    T = w["T"] if T is None else T
+    if name == "fp32_plain":
+        X = synth.piecewise_tucker(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+        return w, X[:T].astype(np.float32)
+    return w, synth.piecewise_tucker_regimes(T, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
 
 
 # ---------------------------------------------------------------------------
@@ -50,8 +69,10 @@ def workload_desc(w):
 # ---------------------------------------------------------------------------
 def query_flops(hits, ranks_out, node_ranks, dims, iters):
     """FLOPs of one range query: partial-hit QR, QR of the stacked factors,
-    initial Gram/eig, `iters` ALS iterations (TTM chains, Grams, eigs at the
-    textbook 9n^3), the core, and the assembly of U1..Up."""
+    initial Gram/eig, `iters` ALS iterations (TTM chains, Grams, eigs), the
+    core, and the assembly of U1..Up.  Symmetric Grams count their packed
+    triangle; an eigenproblem counts its tridiagonalization and the
+    back-transformation of the kept vectors."""
     p = len(ranks_out)
     ro = list(ranks_out)
     q = []
@@ -67,14 +88,20 @@ def query_flops(hits, ranks_out, node_ranks, dims, iters):
         q.append(qi)
     k = [sum(qi[n] for qi in q) for n in range(p)]
     c = [k[0]] + [min(dims[n - 1], k[n]) for n in range(1, p)]
-    eig = lambda n: 9.0 * n ** 3
+    r_keep = list(ro)
+
+    def eig(n, r=None):
+        # Householder tridiagonalization (4/3 n^3) and the back-transformation of
+        # the r kept vectors (2 n^2 r); bisection and inverse iteration are O(n r)
+        return 4.0 / 3.0 * n ** 3 + 2.0 * n * n * (r if r is not None else min(n, max(r_keep)))
     for n in range(1, p):
         Dn = dims[n - 1]
         f += 2.0 * Dn * k[n] ** 2 - 2.0 / 3.0 * min(Dn, k[n]) ** 3      # QR of Phi_n
         for qi in q:
             rest = np.prod(qi) / qi[n]
-            f += 2.0 * c[n] * qi[n] * rest + 2.0 * c[n] ** 2 * rest       # x_n R, Gram
-        f += eig(c[n])
+            f += qi[n] * (qi[n] + 1) * rest                                  # Gram of mat_n(H_i)
+            f += 2.0 * c[n] * qi[n] ** 2 + c[n] * (c[n] + 1) * qi[n]       # R_i M_i R_i^T
+        f += eig(c[n], ro[n])
 
     def chain(qi, order_dims, modes):
         fl, d = 0.0, list(order_dims)
@@ -89,7 +116,7 @@ def query_flops(hits, ranks_out, node_ranks, dims, iters):
             for m in range(1, p):
                 f += 2.0 * ro[m] * qi[m] * c[m]                           # W_im
             f += chain(qi, qi, [(m, ro[m]) for m in range(1, p)])
-        f += 2.0 * k[0] ** 2 * R0 + eig(c[0])
+        f += k[0] * (k[0] + 1) * R0 + eig(c[0], ro[0])
         for n in range(1, p):
             for qi in q:
                 modes = [(0, ro[0])] + [(m, ro[m]) for m in range(1, p) if m != n] + [(n, c[n])]
@@ -98,7 +125,7 @@ def query_flops(hits, ranks_out, node_ranks, dims, iters):
                         f += 2.0 * ro[m] * qi[m] * c[m]
                 f += chain(qi, qi, modes)
             Rn = np.prod(ro) / ro[n]
-            f += 2.0 * c[n] ** 2 * Rn + eig(c[n])
+            f += c[n] * (c[n] + 1) * Rn + eig(c[n], ro[n])
         f += 2.0 * np.prod(ro) * c[p - 1]                                  # core
     for qi, (level, index, lo_n, hi_n, lo, hi, partial) in zip(q, hits):
         ell = hi - lo
@@ -129,7 +156,7 @@ def _oracle_query(args):
 def build_oracle_tree(w, X):
     from oracle.tree import StreamSegmentTree
     t = StreamSegmentTree(w["dims"], w["ranks"], B=w["B"], max_iter=20, tol=0.01)
-    t.build(X)
+    t.build(np.asarray(X, dtype=np.float64))
     return t
 
 
@@ -149,20 +176,31 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def run_reference(args, w):
+def oracle_sample(Q, limit):
+    """Indices of the workload's queries inside the oracle's tree (t_e <=
+    ORACLE_T): on them the tree over the first ORACLE_T slices has the same
+    nodes and hit sets as the full tree (nodes complete at T never change)."""
+    idx = [i for i in range(len(Q)) if Q[i][1] <= ORACLE_T]
+    return idx[:limit]
+
+
+def run_reference(args, name):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    X = synth.piecewise_tucker(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    w = synth.WORKLOADS[name]
+    T_or = min(ORACLE_T, w["T"])
+    _, X = series_of(name, T_or)
     Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
     tree = build_oracle_tree(w, X)
+    sample = [i for i in range(len(Q)) if Q[i][1] <= T_or]
     cores = host_cores()
     per_step = 64
     with oracle_pool(tree, cores) as pool:
-        pool.map(_oracle_query, [tuple(Q[0])] * cores)
+        pool.map(_oracle_query, [tuple(Q[sample[0]])] * cores)
         times, qtimes = [], []
         for s in range(args.warmup + args.steps):
-            idx = [(s * per_step + j) % len(Q) for j in range(per_step)]
+            idx = [sample[(s * per_step + j) % len(sample)] for j in range(per_step)]
             t0 = time.perf_counter()
             res = pool.map(_oracle_query, [tuple(Q[i]) for i in idx], chunksize=1)
             dt = time.perf_counter() - t0
@@ -171,13 +209,14 @@ def run_reference(args, w):
                 qtimes.extend(r[0] for r in res)
     total = sum(times)
     value = per_step * len(times) / total
-    sample = f"{per_step} queries of the workload per step (cycling through its {len(Q)} queries), process pool"
+    desc = (f"{per_step} queries per step, cycling through the {len(sample)} workload queries with t_e <= {T_or}; "
+            f"oracle tree over the first {T_or} slices (built untimed), process pool, BLAS single-threaded")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(w), "impl_note": "FP64 NumPy/LAPACK oracle of the paper's algorithms"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_desc(w, name), "impl_note": "FP64 NumPy/LAPACK oracle of the paper's algorithms"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "latency_ms": {"p50": 1e3 * float(np.percentile(qtimes, 50)), "p99": 1e3 * float(np.percentile(qtimes, 99)),
                        "mode": f"one query per worker, {len(qtimes)} queries"},
@@ -241,17 +280,57 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-# ---------------------------------------------------------------------------
+def fp32_alu_peak(tk, dev_index, sm_max_mhz):
+    """FP32 CUDA-core peak from unit counts and the maximum clock, and the
+    FMA rate the device sustains (tk_probe_fma_rate, CUDA events)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    derived = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    measured = tk.fma_rate("f32", dev_index) / 1e12
+    return derived, measured, sms, mhz
+
+
+def batch_flops(tree, Q, info, w):
+    f = 0.0
+    for i, (ts, te) in enumerate(Q):
+        hits = tree.hit_set(int(ts), int(te))
+        ro = list(info[i].ranks[: tree.p])
+        f += query_flops(hits, ro, list(w["ranks"]), list(w["dims"]), int(info[i].iters))
+    return f
+
+
+def plain_latency(tk, torch, tree, Q, dev, stream, idx, out_d):
+    """The plain GPU method: one query per launch sequence, each timed with
+    CUDA events on the tree's stream."""
+    lat = []
+    with torch.cuda.stream(stream):
+        for i in idx:
+            r = torch.from_numpy(Q[i:i + 1].copy()).to(dev)
+            o = torch.from_numpy(tree.layout(Q[i:i + 1])).to(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.query_batch(r, o, out_d[: int(o[-1])])
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+    return lat
+
+
+def pct(v, q):
+    return float(np.percentile(v, q)) if len(v) else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fp32_plain")
+    ap.add_argument("--workload", default="batched_r16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched-steps", type=int, default=3,
-                    help="timed launches of the 10,000-query batch at 200x150, rank 16 (0: skip)")
+    ap.add_argument("--plain-steps", type=int, default=5,
+                    help="timed launches of the FP32 plain workload's 1000-query batch (0: skip)")
     ap.add_argument("--appends", type=int, default=256,
                     help="single-slice appends timed on the 4-way stream (0: skip)")
     ap.add_argument("--theta-sweep", action="store_true",
@@ -263,11 +342,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the serving run (appends at 1 kHz; 15.36 s covers T 1024 -> 16384)")
     args = ap.parse_args()
-    w = synth.WORKLOADS[args.workload]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        return run_reference(args, w)
+        return run_reference(args, args.workload)
 
     import torch
     import paper_2501_06647_gb300 as tk
@@ -296,12 +374,13 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    X = synth.piecewise_tucker(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    name = args.workload
+    w, X = series_of(name)
     Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
     stream = torch.cuda.Stream(device=dev)
     tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32",
                    device=local, stream=stream)
-    Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+    Xd = torch.from_numpy(X).to(dev)
     torch.cuda.synchronize()
     tb0 = time.perf_counter()
     tree.build(Xd)
@@ -325,7 +404,7 @@ def main():
             step()
     tree.sync()
 
-    # ---- timed region (device time of the query launches; L2 flushed between) --
+    # ---- timed region: device time of the batch launches, L2 flushed between ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = tree.launch_count()
     if dist is not None:
@@ -344,83 +423,91 @@ def main():
     total_ms = sum(step_ms)
     n_q = len(Q)
     total_ms, value = replica_throughput(total_ms, n_q * args.steps, world, dist, dev)
+    clocks = clk.summary()
     tree.sync()
 
-    # ---- per-query latency: one query per launch (plain method) ------------------
-    lat = []
-    one_off = tree.layout(Q[:1])
+    # ---- in-batch latency: launch to each query's completion (GPU global timer) --
     with torch.cuda.stream(stream):
-        for i in range(200):
-            r = torch.from_numpy(Q[i:i + 1].copy()).to(dev)
-            o = torch.from_numpy(tree.layout(Q[i:i + 1])).to(dev)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            tree.query_batch(r, o, out_d)
-            b.record(stream)
-            b.synchronize()
-            lat.append(a.elapsed_time(b))
-    del one_off
-    lat_sorted = sorted(lat)
-    p50 = lat_sorted[len(lat) // 2]
-    p99 = lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]
+        flush.zero_()
+    tree.sync()
+    out_chk, _, info = tree.query_batch_host(Q, offsets, None, with_info=True)
+    t0 = min(f.start_ns for f in info)
+    done_ms = np.array([(f.end_ns - t0) / 1e6 for f in info])
+    job_ms = np.array([(f.end_ns - f.start_ns) / 1e6 for f in info])
 
-    # ---- end to end through the C ABI with host buffers ------------------------
+    # ---- the plain method: one query per launch, on every 50th query ------------
+    plain_idx = list(range(0, n_q, 50))
+    lat = plain_latency(tk, torch, tree, Q, dev, stream, plain_idx, out_d)
+    plain_qps = 1e3 / float(np.mean(lat))
+
+    # ---- end to end through the C ABI with host buffers --------------------------
     host_out = torch.empty(int(offsets[-1]), dtype=torch.float32, pin_memory=True).numpy()
     host_ranges = torch.from_numpy(Q.copy()).pin_memory().numpy()
     host_offs = torch.from_numpy(offsets.copy()).pin_memory().numpy()
     tree.query_batch_host(host_ranges, host_offs, host_out, with_info=False)
     e2e_s = 0.0
-    e2e_steps = max(3, args.steps)
+    e2e_steps = 3
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        ta = time.perf_counter()
         tree.query_batch_host(host_ranges, host_offs, host_out, with_info=False)
-        e2e_s += time.perf_counter() - t0
+        e2e_s += time.perf_counter() - ta
     e2e_value = world * n_q * e2e_steps / e2e_s
 
-    # ---- roofline of the dominant kernel (the batched stitch launch) -------------
-    out_chk, _, info = tree.query_batch_host(Q, offsets, None, with_info=True)
-    flops = 0.0
-    for i, (ts, te) in enumerate(Q):
-        hits = tree.hit_set(int(ts), int(te))
-        ro = list(info[i].ranks[: tree.p])
-        flops += query_flops(hits, ro, list(w["ranks"]), list(w["dims"]), int(info[i].iters))
+    # ---- roofline of the dominant kernel (k_batch answers the whole batch) -------
+    flops = batch_flops(tree, Q, info, w)
+    peak, peak_meas, sms, mhz = fp32_alu_peak(tk, local, clocks.get("sm_max_mhz"))
     avg_launch_s = total_ms / 1e3 / args.steps
     achieved = flops / avg_launch_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_ALU_PEAK_TFLOPS, "traffic": STITCH_BATCH_DRAM_BYTES,
-                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of the k_batch launch of one "
-                                "batch, one ncu capture of this workload (bytes per launch)",
-                "kernel": "k_batch<float> (one launch answers the whole batch)",
+    out_bytes = int(offsets[-1]) * 4
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": BATCH_DRAM_BYTES,
+                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (ncu); "
+                                "null: no capture of this kernel version",
+                "kernel": "k_batch<float> (one persistent launch answers the whole batch, after k_plan)",
                 "flops_per_launch": flops,
-                "peak_note": "FP32 CUDA-core peak derived from 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+                "peak_note": f"FP32 CUDA-core peak from unit counts: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                             f"x {mhz:.0f} MHz; measured FMA rate of this GPU (tk_probe_fma_rate) "
+                             f"{peak_meas:.1f} TFLOP/s, frac of measured {achieved / peak_meas:.4f}",
+                "peak_measured": peak_meas,
+                "hbm_view": {"algorithmic_bytes": out_bytes + tree.arena_bytes(),
+                             "achieved_gbs": (out_bytes + tree.arena_bytes()) / avg_launch_s / 1e9,
+                             "note": "output written + tree read once"}}
 
+    raw_bytes = int(X.nbytes)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(w), "queries_per_step": n_q,
+        "config": {"workload": workload_desc(w, name), "queries_per_step": n_q,
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "tree_build_s": build_s, "tree_arena_bytes": tree.arena_bytes()},
-        "latency_ms": {"p50": p50, "p99": p99, "mode": "one query per launch (plain method), 200 queries"},
-        "batch_latency_ms": total_ms / args.steps,
+                   "tree_arena_bytes": tree.arena_bytes()},
+        "latency_ms": {"p50": pct(done_ms, 50), "p99": pct(done_ms, 99),
+                       "mode": "in-batch: batch launch to each query's completion (GPU global timer), "
+                               f"{n_q} concurrent queries",
+                       "job_p50": pct(job_ms, 50), "job_p99": pct(job_ms, 99)},
+        "plain": {"queries_per_s": plain_qps, "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                  "queries": len(lat), "mode": "one query per launch sequence (every 50th workload query)",
+                  "batched_over_plain": value / plain_qps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(Q.nbytes + offsets.nbytes),
-                "d2h_bytes_per_step": int(offsets[-1]) * 4},
+                "d2h_bytes_per_step": out_bytes},
         "gpu_launches": gpu_launches,
         "roofline": roofline,
-        "clocks": clk.summary(),
+        "tree_build": {"seconds": build_s, "raw_bytes": raw_bytes, "roofline": {
+            "bound": "hbm", "achieved": raw_bytes / build_s / 1e9, "unit": "GB/s",
+            "note": "raw series read once by the leaf kernel; leaves and merges are latency-bound, "
+                    "so this is far below the HBM peak"}},
+        "clocks": clocks,
     }
 
     del out_d, flush
     torch.cuda.empty_cache()
 
-    # ---- serving: interleaved appends and Poisson queries through the server -----
-    batched_sample = None
-    if args.batched_steps > 0:
-        line["batched_r16"], batched_sample = batched_section(tk, torch, dev, local, args.batched_steps)
+    if args.plain_steps > 0:
+        line["plain_r10"] = plain_section(tk, torch, dev, local, args.plain_steps)
     if args.appends > 0:
         line["appends"] = append_section(tk, torch, dev, local, args.appends)
     if args.serve_seconds > 0:
@@ -429,9 +516,7 @@ def main():
     # ---- FP64 oracle on the host cores: cpu_baseline + matched-error check -------
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cpu_section(line, w, X, Q, offsets, tree, out_chk, info, n_q)
-            if batched_sample is not None:
-                batched_accuracy(line["batched_r16"], batched_sample)
+            cpu_section(line, w, X, Q, offsets, tree, out_chk, info)
         except Exception as exc:  # report, do not lose the GPU measurement
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                     "sample": None, "error": f"{type(exc).__name__}: {exc}"}
@@ -443,14 +528,11 @@ def main():
     return 0
 
 
-def batched_section(tk, torch, dev, local, steps):
-    """The batched form at larger shapes: 200x150 slices, T = 8192, ranks 16,
-    leaf 16, FP32; one launch sequence answers 10,000 concurrent queries of
-    log-uniform length 16..8192.  L2 flushed between timed launches.  Returns
-    the report and, for the accuracy check of the CPU leg, the outputs of a
-    sample of short queries."""
-    w = synth.WORKLOADS["batched_r16"]
-    X = synth.piecewise_tucker_regimes(w["T"], w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+def plain_section(tk, torch, dev, local, steps):
+    """The FP32 plain workload (100x100 slices, T = 4096, ranks 10, leaf 16,
+    1000 log-uniform queries): its batched launch and the one-query-per-launch
+    method, L2 flushed between timed launches."""
+    w, X = series_of("fp32_plain")
     Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
     stream = torch.cuda.Stream(device=dev)
     tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local,
@@ -463,65 +545,28 @@ def batched_section(tk, torch, dev, local, steps):
     build_s = time.perf_counter() - t0
     del Xd
     offsets = tree.layout(Q)
-    ranges_d = torch.from_numpy(Q.copy()).to(dev)
-    offsets_d = torch.from_numpy(offsets).to(dev)
-    out_d = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
+    rd = torch.from_numpy(Q.copy()).to(dev)
+    od = torch.from_numpy(offsets).to(dev)
+    out = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    with torch.cuda.stream(stream):
-        flush.zero_()
-        tree.query_batch(ranges_d, offsets_d, out_d)
-    tree.sync()
     ms = []
-    for _ in range(steps):
+    for k in range(steps + 2):
         with torch.cuda.stream(stream):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            tree.query_batch(ranges_d, offsets_d, out_d)
+            tree.query_batch(rd, od, out)
             b.record(stream)
         b.synchronize()
-        ms.append(a.elapsed_time(b))
-    tree.sync()
-    # sample for the accuracy check: queries of length <= 256 (Tucker-ALS from scratch stays cheap)
-    idx = [i for i in range(len(Q)) if Q[i][1] - Q[i][0] <= 256][:8]
-    sample = []
-    for i in idx:
-        ts, te = int(Q[i][0]), int(Q[i][1])
-        flat = out_d[int(offsets[i]):int(offsets[i + 1])].cpu().numpy()
-        G, U = tree.unpack(flat, te - ts)
-        sample.append((X[ts:te], G, U, list(w["ranks"])))
-    out_bytes = int(offsets[-1]) * 4
+        if k >= 2:
+            ms.append(a.elapsed_time(b))
+    lat = plain_latency(tk, torch, tree, Q, dev, stream, list(range(0, len(Q), 5)), out)
     tree.close()
-    del out_d, flush
-    torch.cuda.empty_cache()
-    mean_ms = float(np.mean(ms))
-    return {
-        "workload": f"{w['dims'][0]}x{w['dims'][1]}xT={w['T']} piecewise Tucker rank-{tuple(w['ranks'])}, regime "
-                    f"{w['regime']}, sigma {w['sigma']}, leaf {w['B']}, {w['n_queries']} concurrent log-uniform "
-                    f"queries L in [{w['lo']},{w['hi']}], FP32, max_iter 20, tol 0.01",
-        "queries_per_s": len(Q) / (mean_ms / 1e3), "batch_ms": mean_ms, "steps": steps,
-        "tree_build_s": build_s, "output_bytes_per_batch": out_bytes,
-        "l2": "flushed between timed launches",
-    }, sample
-
-
-def batched_accuracy(rep_, sample):
-    """Paper's metric (Section 8.1) on the sampled queries: ||X - Y|| / ||X - Y_ALS|| - 1,
-    Y_ALS being Tucker-ALS from scratch on the raw subtensor (FP64 oracle)."""
-    from oracle import metrics
-    rel, errs = [], []
-    for Xs, G, U, ranks in sample:
-        Xs = np.asarray(Xs, dtype=np.float64)
-        G = np.float64(G)
-        U = [np.float64(u) for u in U]
-        Ga, Ua, _, _ = metrics.from_scratch(Xs, ranks)
-        rel.append(metrics.paper_relative_error(Xs, G, U, Ga, Ua))
-        errs.append(metrics.relative_error(Xs, G, U))
-    rep_["accuracy"] = {"queries": len(rel), "mean_paper_relative_error": float(np.mean(rel)) if rel else None,
-                        "max_paper_relative_error": float(np.max(rel)) if rel else None,
-                        "mean_rel_err": float(np.mean(errs)) if errs else None,
-                        "metric": "||X - Y|| / ||X - Y_ALS|| - 1 against FP64 Tucker-ALS from scratch, "
-                                  "queries of length <= 256"}
+    qps = len(Q) / (np.mean(ms) / 1e3)
+    return {"workload": workload_desc(w, "fp32_plain"), "batch_ms": float(np.mean(ms)), "queries_per_s": qps,
+            "plain_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "queries": len(lat)},
+            "plain_queries_per_s": 1e3 / float(np.mean(lat)), "batched_over_plain": qps * float(np.mean(lat)) / 1e3,
+            "tree_build_s": build_s}
 
 
 def theta_sweep(tk, torch, dev, local, thetas=((1, 2), (7, 10), (9, 10))):
@@ -785,36 +830,42 @@ def serving_section(tk, torch, dev, local, seconds):
     }
 
 
-def cpu_section(line, w, X, Q, offsets, tree, out_chk, info, n_q):
-    """FP64 oracle on the host cores: cpu_baseline and the matched-error check."""
-    tree_o = build_oracle_tree(w, X)
+def cpu_section(line, w, X, Q, offsets, tree, out_chk, info):
+    """FP64 oracle on the host cores (cpu_baseline) and the matched-error
+    check of the batched FP32 answers, on the workload's queries with t_e <=
+    ORACLE_T (the oracle's tree covers the first ORACLE_T slices)."""
+    tree_o = build_oracle_tree(w, X[:ORACLE_T])
     cores = host_cores()
-    sample = list(range(0, n_q, max(1, n_q // 400)))[:400]
+    sample = oracle_sample(Q, 400)
     with oracle_pool(tree_o, cores) as pool:
-        pool.map(_oracle_query, [tuple(Q[0])] * cores)
+        pool.map(_oracle_query, [tuple(Q[sample[0]])] * cores)
         t0 = time.perf_counter()
         res = pool.map(_oracle_query, [tuple(Q[i]) for i in sample], chunksize=1)
         wall = time.perf_counter() - t0
     line["cpu_baseline"] = {"value": len(sample) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{len(sample)} of the {n_q} workload queries (every "
-                                      f"{max(1, n_q // 400)}th), tree prebuilt, process pool, "
-                                      "BLAS single-threaded per worker"}
+                            "sample": f"{len(sample)} workload queries with t_e <= {ORACLE_T}; oracle tree over the "
+                                      f"first {ORACLE_T} slices (same nodes and hit sets there), built untimed; "
+                                      "process pool, BLAS single-threaded per worker"}
     from oracle import metrics
     eg, eo, dd = [], [], []
-    for j, i in enumerate(sample[:100]):
+    for j, i in enumerate(sample[:150]):
         ts, te = int(Q[i][0]), int(Q[i][1])
         G, U = tree.unpack(out_chk[offsets[i]:offsets[i + 1]], te - ts)
         r = list(info[i].ranks[: tree.p])
         G = np.float64(G[tuple(slice(0, x) for x in r)])
         U = [np.float64(u[:, :x]) for u, x in zip(U, r)]
-        Xs = X[ts:te]
+        Xs = np.asarray(X[ts:te], dtype=np.float64)
         eg.append(metrics.relative_error(Xs, G, U))
         eo.append(metrics.relative_error(Xs, res[j][1], res[j][2]))
         dd.append(metrics.model_distance(G, U, res[j][1], res[j][2]) / np.linalg.norm(Xs))
+    eg, eo = np.array(eg), np.array(eo)
     line["accuracy"] = {"queries": len(eg), "mean_rel_err_gpu": float(np.mean(eg)),
                         "mean_rel_err_oracle_fp64": float(np.mean(eo)),
-                        "max_abs_err_diff": float(np.max(np.abs(np.array(eg) - np.array(eo)))),
+                        "mean_rel_err_relative_diff": float(abs(np.mean(eg) - np.mean(eo)) / np.mean(eo)),
+                        "max_abs_err_diff": float(np.max(np.abs(eg - eo))),
                         "max_model_distance_rel": float(np.max(dd)),
+                        "matched_vs_plain": "the batched launch and the one-query-per-launch method run the same "
+                                            "kernels on the same tree: identical errors",
                         "note": "both with tol 0.01; iteration counts may differ near the threshold"}
 
 

@@ -96,6 +96,7 @@ typedef struct tk_query_info {
   int64_t init_cycles;              /* stage 2: QR of the stacked factors and the HOSVD start */
   int64_t als_cycles;               /* stage 3: the ALS iterations of Algorithm 2 */
   int64_t out_cycles;               /* stage 4: core and factor assembly into the output */
+  int64_t start_ns, end_ns;         /* GPU global timer when the query's job started and ended */
 } tk_query_info;
 
 typedef struct tk_tree tk_tree;
@@ -177,6 +178,13 @@ int tk_sync(tk_tree* t);
 int64_t tk_launch_count(const tk_tree* t);
 
 const char* tk_strerror(int code);
+
+/* Measurement helper with no counterpart in the paper: the rate of fused
+ * multiply-adds in dtype (TK_F32 or TK_F64) that device sustains, in FLOP/s
+ * (2 per FMA), from a kernel of independent FMA chains on every SM timed with
+ * CUDA events (best of 3 after a warm-up).  It is the denominator of the
+ * engine's arithmetic roofline.  Synchronous; allocates a small buffer. */
+int tk_probe_fma_rate(int dtype, int device, double* flops_per_s);
 
 /* Copy of the configuration the tree was created with. */
 int tk_tree_get_config(const tk_tree* t, tk_config* out);

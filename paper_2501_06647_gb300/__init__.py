@@ -47,7 +47,8 @@ class TkQueryInfo(ctypes.Structure):
                 ("eig_max_order", ctypes.c_int32), ("device_cycles", ctypes.c_int64),
                 ("eig_cycles", ctypes.c_int64), ("qr_cycles", ctypes.c_int64),
                 ("hit_cycles", ctypes.c_int64), ("init_cycles", ctypes.c_int64),
-                ("als_cycles", ctypes.c_int64), ("out_cycles", ctypes.c_int64)]
+                ("als_cycles", ctypes.c_int64), ("out_cycles", ctypes.c_int64),
+                ("start_ns", ctypes.c_int64), ("end_ns", ctypes.c_int64)]
 
 
 class TkServerConfig(ctypes.Structure):
@@ -84,6 +85,7 @@ _SIGS = {
     "tk_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "tk_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "tk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "tk_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "tk_range_query_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p]),
@@ -160,6 +162,14 @@ def _ptr(x):
     if not x.flags["C_CONTIGUOUS"]:
         raise ValueError("array must be C-contiguous")
     return ctypes.c_void_p(x.ctypes.data)
+
+
+def fma_rate(dtype="f32", device=0):
+    """Measured FMA throughput of the device in FLOP/s (tk_probe_fma_rate)."""
+    v = ctypes.c_double()
+    _check(lib().tk_probe_fma_rate(TK_F64 if dtype == "f64" else TK_F32, int(device), ctypes.byref(v)),
+           "tk_probe_fma_rate")
+    return v.value
 
 
 class Tree:

@@ -113,7 +113,19 @@ __device__ void ttm(const S* X, const int* d, int p, int n, const S* M, int mrs,
 #pragma unroll
     for (int c = 0; c < CH; ++c) acc[c] = 0;
     if (a0 + CH <= a) {
-      for (int j = 0; j < dn; ++j) {
+      // eight loads of X issued before their FMAs, so that operands in
+      // global memory overlap their latency
+      int j = 0;
+      for (; j + 8 <= dn; j += 8) {
+        S x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = xp[(j + u) * inner];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int c = 0; c < CH; ++c) acc[c] += mp[c * mrs + (j + u) * mcs] * x[u];
+      }
+      for (; j < dn; ++j) {
         const S x = xp[j * inner];
 #pragma unroll
         for (int c = 0; c < CH; ++c) acc[c] += mp[c * mrs + j * mcs] * x;
@@ -169,7 +181,18 @@ __device__ void mode_gram(const S* X, const int* d, int p, int n, S* A, int lda,
       for (int o = 0; o < outer; ++o) {
         const S* pa = X + (o * dn + a) * inner;
         const S* pb = X + (o * dn + b) * inner;
-        for (int i = 0; i < inner; ++i) acc += pa[i] * pb[i];
+        int i = 0;
+        for (; i + 4 <= inner; i += 4) {
+          S xa[4], xb[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            xa[u] = pa[i + u];
+            xb[u] = pb[i + u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc += xa[u] * xb[u];
+        }
+        for (; i < inner; ++i) acc += pa[i] * pb[i];
       }
       if (accumulate) {
         A[a * lda + b] += acc;
@@ -189,6 +212,27 @@ __device__ void mode_gram(const S* X, const int* d, int p, int n, S* A, int lda,
   G::sync();
 }
 
+// A (n x n, lda) += P Q^T for P, Q of n x k (row-major, leading dimensions
+// ldp, ldq) whose product is symmetric in exact arithmetic: each entry a <= b
+// is computed once and written to (a, b) and (b, a), so A stays exactly
+// symmetric.  One thread per entry of the packed upper triangle.
+template <class G, class S>
+__device__ void sym_accum(int n, int k, const S* P, int ldp, const S* Q, int ldq, S* A, int lda) {
+  const int npairs = n * (n + 1) / 2;
+  for (int idx = G::rank(); idx < npairs; idx += G::size()) {
+    int a = (int)((2.f * n + 1.f - sqrtf((2.f * n + 1.f) * (2.f * n + 1.f) - 8.f * idx)) * 0.5f);
+    if (a < 0) a = 0;
+    while (a > 0 && a * (2 * n - a + 1) / 2 > idx) --a;
+    while ((a + 1) * (2 * n - a) / 2 <= idx) ++a;
+    const int b = idx - a * (2 * n - a + 1) / 2 + a;
+    S acc = 0;
+    for (int t = 0; t < k; ++t) acc += P[a * ldp + t] * Q[b * ldq + t];
+    A[a * lda + b] += acc;
+    if (a != b) A[b * lda + a] += acc;
+  }
+  G::sync();
+}
+
 // C (M x N) = A (M x K) * B (K x N) with general strides; accumulate: C +=.
 template <class G, class S>
 __device__ void gemm(int M, int N, int K, const S* A, int ars, int acs, const S* B, int brs, int bcs, S* C,
@@ -199,7 +243,18 @@ __device__ void gemm(int M, int N, int K, const S* A, int ars, int acs, const S*
   int i = idx / N, j = idx - (idx / N) * N;
   for (; idx < M * N; idx += nt) {
     S acc = 0;
-    for (int k = 0; k < K; ++k) acc += A[i * ars + k * acs] * B[k * brs + j * bcs];
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+      S xa[4], xb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xa[u] = A[i * ars + (k + u) * acs];
+        xb[u] = B[(k + u) * brs + j * bcs];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += xa[u] * xb[u];
+    }
+    for (; k < K; ++k) acc += A[i * ars + k * acs] * B[k * brs + j * bcs];
     if (accumulate) C[i * crs + j * ccs] += acc;
     else C[i * crs + j * ccs] = acc;
     j += dj;
@@ -708,31 +763,25 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
     const S beta = sc[0];
     if (beta == S(0)) continue;
     // p = beta A' v on the trailing block A' (rows and columns >= m0); with
-    // more threads than rows, `sp` threads share a row and combine in pv
+    // more threads than rows, g consecutive lanes (a power of two <= 32)
+    // share a row and combine by shuffles
     {
-      int sp = nt / len;
-      sp = sp > 4 ? 4 : sp;
-      if (sp < 2) {
+      int g = 1;
+      while (g < 32 && 2 * g * len <= nt) g *= 2;
+      if (g == 1) {
         for (int i = m0 + tid; i < n; i += nt) {
           S acc = 0;
           for (int j = m0; j < n; ++j) acc += A[j * lda + i] * v[j];
           pv[i] = beta * acc;
         }
       } else {
-        const int t = tid % len, part = tid / len;
-        if (part < sp) {
-          const int i = m0 + t;
-          const int j0 = m0 + (len * part) / sp, j1 = m0 + (len * (part + 1)) / sp;
-          S acc = 0;
-          for (int j = j0; j < j1; ++j) acc += A[j * lda + i] * v[j];
-          wsc[part * n + i] = acc;
-        }
-        G::sync();
-        for (int i = m0 + tid; i < n; i += nt) {
-          S acc = 0;
-          for (int q = 0; q < sp; ++q) acc += wsc[q * n + i];
-          pv[i] = beta * acc;
-        }
+        const int row = tid / g, sub = tid & (g - 1);
+        const int i = m0 + row;
+        S acc = 0;
+        if (row < len)
+          for (int j = m0 + sub; j < n; j += g) acc += A[i * lda + j] * v[j];  // row i: consecutive lanes, consecutive j
+        for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (row < len && sub == 0) pv[i] = beta * acc;
       }
     }
     G::sync();

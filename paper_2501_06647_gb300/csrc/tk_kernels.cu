@@ -145,3 +145,65 @@ int tk_launch_hitset(const TkTreeView& tv, int n, const int64_t* ranges, tk_hit*
   k_hitset<<<(n + nt - 1) / nt, nt, 0, stream>>>(tv, n, ranges, out, cap, counts);
   return cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
 }
+
+// ---- FMA-rate probe ----------------------------------------------------------
+// Every thread runs 8 independent chains of fused multiply-adds (enough in
+// flight to cover the FMA latency on every scheduler); the result is written
+// so that the chains are not optimized away.
+namespace {
+
+template <class S>
+__global__ void __launch_bounds__(256) k_fma_rate(S* out, int iters, S a, S b) {
+  S x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = S(threadIdx.x) * S(1e-7) + S(i);
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+  }
+  S s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class S> int fma_rate(int device, double* flops_per_s) {
+  int sms = 0;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return TK_ERR_CUDA;
+  const int blocks = 8 * sms, threads = 256;
+  const int iters = sizeof(S) == 8 ? 64 : 2048;
+  S* out = nullptr;
+  if (cudaMalloc(&out, sizeof(S) * (size_t)blocks * threads) != cudaSuccess) return TK_ERR_NOMEM;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first run is a warm-up
+    cudaEventRecord(e0);
+    k_fma_rate<S><<<blocks, threads>>>(out, iters, S(0.9999), S(1e-6));
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  const int rc = cudaGetLastError() == cudaSuccess ? TK_OK : TK_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (rc == TK_OK) *flops_per_s = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int tk_probe_fma_rate(int dtype, int device, double* flops_per_s) {
+  if (!flops_per_s || (dtype != TK_F64 && dtype != TK_F32)) return TK_ERR_ARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  const int rc = dtype == TK_F64 ? fma_rate<double>(device, flops_per_s) : fma_rate<float>(device, flops_per_s);
+  if (prev >= 0) cudaSetDevice(prev);
+  return rc;
+}

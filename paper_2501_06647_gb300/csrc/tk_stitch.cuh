@@ -187,6 +187,13 @@ __device__ inline int recall_count(const TkTreeView& tv, const TkEpoch& ep, int6
 
 __device__ inline void set_err(int* status, int code) { atomicCAS(status, 0, code); }
 
+// The GPU's global nanosecond timer (the same clock on every SM).
+__device__ __forceinline__ int64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (int64_t)t;
+}
+
 // Output-rank clamp of a stitch: r_n' = min(r_n, extent_n, sum_i min(q_in,
 // prod_{m!=n} q_im)), then r_n' <= prod_{m!=n} r_m' to a fixpoint.
 __device__ inline void stitch_ranks(int p, const int* rq, const int64_t* ext, const HitRec* hits, int nh, int* ro) {
@@ -237,6 +244,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   WarpSm<S>& sm = *reinterpret_cast<WarpSm<S>*>(wsm_raw);
   StitchCtx<S>& cx = sm.ctx;
   const long long t_start = clock64();
+  const int64_t ns_start = global_ns();
   HitRec* hits = reinterpret_cast<HitRec*>(ws);  // Recall writes here; copied to the arena below
   const int hits_elems = (int)((TK_MAXH * (int64_t)TK_HITREC_BYTES + sizeof(S) - 1) / sizeof(S));
   const int p = tv.p;
@@ -349,6 +357,11 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
         s *= e;
       }
       if (s > tb) tb = s;
+    }
+    for (int n = 0; n < p; ++n) {  // the init's per-hit Gram and its product with R_n's block
+      const int64_t g = (int64_t)cx.qmax[n] * cx.qmax[n], rm = (int64_t)cx.c[n] * cx.qmax[n];
+      tb = g > tb ? g : tb;
+      tb = rm > tb ? rm : tb;
     }
     cx.b0 = take(tb);
     cx.b1 = take(tb);
@@ -557,14 +570,18 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     }
     for (int idx = lane; idx < cn * cn; idx += nt) A[idx] = 0;
     G::sync();
-    // init: sum_i modegram_n(H~_i x_n R_n[:, blk i]) = Q_n^T mat_n(Y~) mat_n(Y~)^T Q_n
+    // init: Q_n^T mat_n(Y~) mat_n(Y~)^T Q_n = sum_i R_i M_i R_i^T, with
+    // R_i = R_n[:, blk i] (c_n x q_in) and M_i = mat_n(H~_i) mat_n(H~_i)^T
+    // (q_in x q_in): the Gram of mat_n(H~_i x_n R_i) without forming it
     for (int i = 0; i < nh; ++i) {
       const HitRec& h = hits[i];
       for (int m = 0; m < p; ++m) dims[m] = h.q[m];
-      S* b0 = cx.b0;
-      ttm<G, S>(reinterpret_cast<S*>(h.core), dims, p, n, R + h.koff[n], kn, 1, cn, b0, false);
-      dims[n] = cn;
-      mode_gram<G, S>(b0, dims, p, n, A, cn, true);
+      const int qn = h.q[n];
+      S* Mi = cx.b0;
+      S* RM = cx.b1;
+      mode_gram<G, S>(reinterpret_cast<S*>(h.core), dims, p, n, Mi, qn, false);
+      gemm<G, S>(cn, qn, qn, R + h.koff[n], kn, 1, Mi, qn, 1, RM, qn, 1, false);
+      sym_accum<G, S>(cn, qn, RM, qn, R + h.koff[n], kn, A, cn);
     }
     eig(n, cn, cx.E[n], cx.ro[n]);
   }
@@ -738,6 +755,8 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       info->init_cycles = (int64_t)(t_init - t_hits);
       info->als_cycles = (int64_t)(t_als - t_init);
       info->out_cycles = (int64_t)(clock64() - t_als);
+      info->start_ns = ns_start;
+      info->end_ns = global_ns();
     }
   }
   G::sync();

@@ -22,7 +22,7 @@ def test_reference_arm_prints_one_contract_line():
         assert k in line, k
     assert line["impl"] == "reference" and line["unit"] == "queries/s" and line["higher_is_better"] is True
     assert line["steps"] == 1 and line["warmup"] >= 3 and line["value"] > 0
-    assert line["config"]["workload"].startswith("fp32_plain: 100x100xT=4096")
+    assert line["config"]["workload"].startswith("batched_r16: 200x150xT=8192")
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
