@@ -55,6 +55,16 @@ typedef enum tk_status {
 } tk_status;
 
 typedef enum tk_dtype { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
+/* Arithmetic of the leaf blocks' Gram matrices (the dense contractions of
+ * Tucker-ALS over raw data, Section 2), for FP32 trees:
+ *   TK_MATH_AUTO       tensor cores with split TF32 products (hi*hi + hi*lo +
+ *                      lo*hi, FP32 accumulation), FP32 accuracy (FP64 trees:
+ *                      FP64 CUDA cores);
+ *   TK_MATH_CUDA_CORES FP32 (or FP64) CUDA cores;
+ *   TK_MATH_TF32       tensor cores with one TF32 product (FP32 accumulation):
+ *                      faster, about 1e-3 relative error per product.
+ * Everything else (the stitch, eigensolvers, QR) runs in the tree's dtype. */
+typedef enum tk_math { TK_MATH_AUTO = 0, TK_MATH_CUDA_CORES = 1, TK_MATH_TF32 = 2 } tk_math;
 typedef enum tk_io { TK_IO_DEVICE = 0, TK_IO_HOST = 1 } tk_io;
 
 /* Tree configuration.  Hyperparameter defaults follow Section 8.1 of the
@@ -70,6 +80,7 @@ typedef struct tk_config {
   int32_t dtype;                    /* tk_dtype */
   int32_t device;                   /* CUDA device ordinal */
   int64_t hbm_budget;               /* device bytes the tree may hold (0: no limit) */
+  int32_t math;                     /* tk_math of the leaf Grams (TK_MATH_TF32: FP32 trees only) */
 } tk_config;
 
 /* One node of a hit set (Algorithm 1, Section 5.1), in time order. */

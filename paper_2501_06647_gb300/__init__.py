@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libtucket.so")
 MAX_MODES = 8
 
 TK_F64, TK_F32 = 0, 1
+MATH = {"auto": 0, "cuda_cores": 1, "tf32": 2}
 TK_IO_DEVICE, TK_IO_HOST = 0, 1
 
 _ERR = {
@@ -32,7 +33,7 @@ class TkConfig(ctypes.Structure):
                 ("ranks", ctypes.c_int32 * MAX_MODES), ("leaf_slices", ctypes.c_int32),
                 ("theta_num", ctypes.c_int32), ("theta_den", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("dtype", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_int64)]
+                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_int64), ("math", ctypes.c_int32)]
 
 
 class TkHit(ctypes.Structure):
@@ -178,11 +179,12 @@ class Tree:
     dims are the non-temporal sizes D_2..D_p, ranks the build ranks r_1..r_p,
     leaf_slices the slices per leaf block, theta the pruning threshold as a
     fraction (num, den), dtype "f64" or "f32", hbm_budget the device bytes the
-    tree may hold (0: no limit).
+    tree may hold (0: no limit), math the arithmetic of the leaf Grams ("auto":
+    split-TF32 tensor cores for FP32 trees, "cuda_cores", or "tf32").
     """
 
     def __init__(self, dims, ranks, leaf_slices=1, theta=(7, 10), max_iter=20, tol=0.01, dtype="f32",
-                 device=0, stream=None, hbm_budget=0):
+                 device=0, stream=None, hbm_budget=0, math="auto"):
         self.dims = tuple(int(d) for d in dims)
         self.ranks = tuple(int(r) for r in ranks)
         self.p = len(self.ranks)
@@ -204,6 +206,7 @@ class Tree:
         cfg.dtype = TK_F64 if dtype == "f64" else TK_F32
         cfg.device = int(device)
         cfg.hbm_budget = int(hbm_budget)
+        cfg.math = MATH[math]
         self.cfg = cfg
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()

@@ -12,6 +12,7 @@
 
 #include "tk_device.cuh"
 #include "tk_internal.h"
+#include "tk_tc.cuh"
 
 namespace {
 
@@ -57,7 +58,8 @@ struct tk_tree {
   DevBuf ws_stitch, ws_leaf, status;
   int64_t ws_stitch_per_cta = 0, ws_leaf_per_cta = 0;
   int ws_stitch_ctas = 0, ws_leaf_ctas = 0;
-  int nsm_stitch = 0, nsa_leaf = 0, nsv_leaf = 0;
+  int nsm_stitch = 0, nsa_leaf = 0, nsv_leaf = 0, tc_leaf = 0;
+  int64_t tc_bytes_leaf = 0;
   int sm_count = 0;
   // staging for host io and batch metadata
   DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
@@ -319,7 +321,7 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
 // Workspace of one leaf cluster (see TkLeafLayout), with every rank at its
 // build value and the block at its full B slices: bounds for any block.
 // nsa / nsv: the shared-memory capacities (orders) of the eigensolvers.
-TkLeafLayout leaf_layout(const tk_tree* t, int nsa, int nsv, int64_t* per_cluster) {
+TkLeafLayout leaf_layout(const tk_tree* t, int nsa, int nsv, int tc, int64_t tc_bytes, int64_t* per_cluster) {
   TkLeafLayout ly{};
   const int p = t->p;
   const int CL = TK_LEAF_CL;
@@ -373,6 +375,8 @@ TkLeafLayout leaf_layout(const tk_tree* t, int nsa, int nsv, int64_t* per_cluste
   }
   ly.nsa = nsa;
   ly.nsv = nsv;
+  ly.tc = tc;
+  ly.tc_bytes = tc_bytes;
   ly.neig = (int)neig;
   ly.rmax = 1;
   for (int n = 0; n < p; ++n) ly.rmax = std::max<int>(ly.rmax, (int)r[n]);
@@ -410,18 +414,42 @@ int stitch_warps(const tk_tree* t) { (void)t; return 8; }
 // arrays for orders below the tridiagonal method's, and A (the only n x n
 // array of the tridiagonal method) for the largest order that fits next to
 // the contraction buffers in a CTA's shared memory.
-void pick_nsm_leaf(const tk_tree* t, int* nsa, int* nsv) {
+//
+// Grams on the tensor cores (FP32 trees, unless the configuration asks for
+// CUDA cores): their staging buffers alias the contraction buffers and get
+// what shared memory the eigensolver leaves, up to 64 columns per chunk of
+// the largest order; the kernel then asks for at least 116 KB, so that one
+// CTA per SM holds tensor memory (a second CTA's allocation would wait).
+void pick_nsm_leaf(const tk_tree* t, int* nsa, int* nsv, int* tc, int64_t* tc_bytes) {
   int need = t->cfg.leaf_slices, rmax = 1;
   for (int n = 1; n < t->p; ++n) need = std::max<int>(need, (int)t->cfg.dims[n]);
   for (int n = 0; n < t->p; ++n) rmax = std::max<int>(rmax, t->cfg.ranks[n]);
   rmax = std::min(rmax, need);
   *nsv = std::max(2, std::min(need, tk::kTrdMinOrder - 1));
   const size_t limit = 227 * 1024 - 512;
-  const size_t base = tk_leaf_smem_bytes(t->cfg.dtype, 0, *nsv, need, rmax);
+  const size_t base = tk_leaf_smem_bytes(t->cfg.dtype, 0, *nsv, need, rmax, 0);
   int a = 0;
   if (base < limit) a = (int)std::sqrt((double)(limit - base - 16) / (double)t->es);
   *nsa = std::max(*nsv, std::min(need, a));
-  while (*nsa > *nsv && tk_leaf_smem_bytes(t->cfg.dtype, *nsa, *nsv, need, rmax) > limit) --*nsa;
+  while (*nsa > *nsv && tk_leaf_smem_bytes(t->cfg.dtype, *nsa, *nsv, need, rmax, 0) > limit) --*nsa;
+  *tc = 0;
+  *tc_bytes = 0;
+  if (t->cfg.dtype != TK_F32 || t->cfg.math == TK_MATH_CUDA_CORES) return;
+  int dtc = 0;  // largest Gram order on the tensor-core path
+  for (int n = 0; n < t->p; ++n) {
+    const int d = n == 0 ? t->cfg.leaf_slices : (int)t->cfg.dims[n];
+    if (d <= tk::kTcMaxD) dtc = std::max(dtc, d);
+  }
+  if (dtc == 0) return;
+  const size_t with = tk_leaf_smem_bytes(t->cfg.dtype, *nsa, *nsv, need, rmax, 0);
+  const size_t rest = with - tk_leaf_contraction_bytes(t->cfg.dtype, need, rmax);
+  const int64_t want = (int64_t)4 * 16 * tk::tc_lbo(dtc);  // 64 columns per chunk
+  int64_t bytes = std::min<int64_t>(want, (int64_t)limit - (int64_t)rest);
+  bytes = std::max<int64_t>(bytes, (int64_t)(116 * 1024) - (int64_t)rest);
+  bytes &= ~(int64_t)15;
+  if (tk::tc_chunk(dtc, bytes, TK_NT) < 8 || rest + (size_t)bytes > limit) return;
+  *tc = t->cfg.math == TK_MATH_TF32 ? 2 : 1;
+  *tc_bytes = bytes;
 }
 
 // Stitch workspace: one chunk per CTA of the grid.
@@ -442,9 +470,9 @@ int ensure_ws_stitch(tk_tree* t, int want_ctas) {
 
 // Leaf workspace: one chunk per cluster of the grid.
 int ensure_ws_leaf(tk_tree* t, int want_clusters, TkLeafLayout* ly) {
-  if (t->nsa_leaf == 0) pick_nsm_leaf(t, &t->nsa_leaf, &t->nsv_leaf);
+  if (t->nsa_leaf == 0) pick_nsm_leaf(t, &t->nsa_leaf, &t->nsv_leaf, &t->tc_leaf, &t->tc_bytes_leaf);
   int64_t per = 0;
-  *ly = leaf_layout(t, t->nsa_leaf, t->nsv_leaf, &per);
+  *ly = leaf_layout(t, t->nsa_leaf, t->nsv_leaf, t->tc_leaf, t->tc_bytes_leaf, &per);
   int n = std::max(1, want_clusters);
   if (per != t->ws_leaf_per_cta || n > t->ws_leaf_ctas) {
     n = std::max(n, t->ws_leaf_ctas);
@@ -494,11 +522,11 @@ int grid_for(tk_tree* t, int njobs) {
 // elements), each of `ell` slices: one cluster per block, persistent.
 int run_leaves(tk_tree* t, const void* raw, int64_t block_stride, int64_t first, int njobs, int ell) {
   if (njobs <= 0) return TK_OK;
-  if (t->nsa_leaf == 0) pick_nsm_leaf(t, &t->nsa_leaf, &t->nsv_leaf);
+  if (t->nsa_leaf == 0) pick_nsm_leaf(t, &t->nsa_leaf, &t->nsv_leaf, &t->tc_leaf, &t->tc_bytes_leaf);
   int64_t per = 0;
-  const TkLeafLayout probe = leaf_layout(t, t->nsa_leaf, t->nsv_leaf, &per);
-  int maxc = tk_leaf_max_clusters(t->cfg.dtype,
-                                  tk_leaf_smem_bytes(t->cfg.dtype, probe.nsa, probe.nsv, probe.neig, probe.rmax));
+  const TkLeafLayout probe = leaf_layout(t, t->nsa_leaf, t->nsv_leaf, t->tc_leaf, t->tc_bytes_leaf, &per);
+  int maxc = tk_leaf_max_clusters(t->cfg.dtype, tk_leaf_smem_bytes(t->cfg.dtype, probe.nsa, probe.nsv, probe.neig,
+                                                                   probe.rmax, probe.tc_bytes));
   if (maxc < 1) maxc = 1;
   const int ncl = std::min(njobs, maxc);
   TkLeafLayout ly{};
@@ -640,6 +668,8 @@ int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out) {
     return TK_ERR_ARG;
   if (cfg->max_iter < 1 || (cfg->dtype != TK_F64 && cfg->dtype != TK_F32)) return TK_ERR_ARG;
   if (cfg->hbm_budget < 0) return TK_ERR_ARG;
+  if (cfg->math < TK_MATH_AUTO || cfg->math > TK_MATH_TF32 || (cfg->math == TK_MATH_TF32 && cfg->dtype != TK_F32))
+    return TK_ERR_ARG;
   for (int n = 0; n < cfg->p; ++n)
     if (cfg->ranks[n] < 1 || cfg->ranks[n] > 4096) return TK_ERR_ARG;
   for (int n = 1; n < cfg->p; ++n)

@@ -91,6 +91,8 @@ struct TkLeafLayout {
   int nsv;                 // largest order whose Jacobi arrays (V, rotations) are in shared memory
   int neig;                // largest Gram order of a block
   int rmax;                // largest rank
+  int tc;                  // Grams on the tensor cores: 0 no, 1 split TF32 (FP32 accuracy), 2 TF32
+  int64_t tc_bytes;        // shared-memory bytes of the tensor-core staging buffers
 };
 
 // Launchers (tk_kernels.cu, tk_leaf.cu).  All asynchronous on `stream`.
@@ -98,7 +100,8 @@ struct TkLeafLayout {
 int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t block_stride,
                    int64_t first_block, int njobs, int ell, const TkWorkspace& ws,
                    const TkLeafLayout& ly, int nclusters, cudaStream_t stream);
-size_t tk_leaf_smem_bytes(int dtype, int nsa, int nsv, int neig, int rmax);
+size_t tk_leaf_smem_bytes(int dtype, int nsa, int nsv, int neig, int rmax, int64_t tc_bytes);
+size_t tk_leaf_contraction_bytes(int dtype, int neig, int rmax);
 int tk_leaf_max_clusters(int dtype, size_t smem);
 int tk_launch_merge(int dtype, const TkTreeView& tv, int level, int64_t k0, int njobs,
                     const TkWorkspace& ws, int grid, cudaStream_t stream);

@@ -18,8 +18,12 @@
 // The arithmetic of every stored value depends on the cluster size only, not
 // on how many blocks a launch decomposes, so tree build and appends store the
 // same bits.
+#include <algorithm>
+#include <type_traits>
+
 #include "tk_device.cuh"
 #include "tk_internal.h"
+#include "tk_tc.cuh"
 
 namespace tk {
 
@@ -397,10 +401,50 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
   S* sV = reinterpret_cast<S*>(smem_raw + off);
   off += align16(sizeof(S) * (size_t)nsv * nsv);
   S* tile = reinterpret_cast<S*>(smem_raw + off);
+  // the tensor-core Gram's staging buffers alias tile, stage and us: the Gram
+  // phases and the contractions that use those never overlap
+  unsigned char* tc_stage = smem_raw + off;
   off += align16(sizeof(S) * (size_t)kKC * (((ly.neig + 3) & ~3) + 4));
   S* stage = reinterpret_cast<S*>(smem_raw + off);
   off += align16(sizeof(S) * (size_t)kStage);
   S* us = reinterpret_cast<S*>(smem_raw + off);
+
+  // tensor memory and the mbarriers of the tensor-core Grams (FP32 trees)
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  constexpr bool kF32 = std::is_same<S, float>::value;
+  const bool tc_on = kF32 && ly.tc != 0;
+  TcState st;
+  st.tmem = 0;
+  st.mbar = s_mbar;
+  st.phase[0] = st.phase[1] = 0;
+  st.pending[0] = st.pending[1] = 0;
+  st.failed = 0;
+  if (tc_on) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_mbar[0], 1);
+      mbar_init(&s_mbar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(&s_tmem, kTcTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    st.tmem = s_tmem;
+  }
+  // Gram of the columns [c0, c1) of a matricization on the tensor cores when
+  // that path is on and the order fits it, else on the CUDA cores
+  auto gram = [&](const S* Xg, int D, int64_t inner, int64_t c0, int64_t c1, S* Ag, int lda) {
+    bool done = false;
+    if constexpr (kF32) {
+      // (orders below 32 stay on the CUDA cores: too little work per chunk)
+      const int kc = tc_on && D >= 32 && D <= kTcMaxD ? tc_chunk(D, ly.tc_bytes, blockDim.x) : 0;
+      if (kc > 0)
+        done = gram_tc(reinterpret_cast<const float*>(Xg), D, inner, c0, c1, reinterpret_cast<float*>(Ag), lda,
+                       tc_stage, kc, st, ly.tc == 1, wsd.status);
+    }
+    if (!done) gram_cols<S>(Xg, D, inner, c0, c1, Ag, lda, tile);
+  };
 
   S* wc = reinterpret_cast<S*>(wsd.base) + (int64_t)cid * wsd.per_cta;  // the cluster's chunk
   S* wt = wc + ly.cta + (int64_t)crank * ly.cta_stride;                 // this CTA's part
@@ -464,8 +508,8 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
     for (int n = 1; n < p; ++n) {
       const int64_t ncols = N / xd[n];
       const int64_t DD = (int64_t)xd[n] * xd[n];
-      gram_cols<S>(X, xd[n], prod64(xd, n + 1, p), ncols * crank / TK_LEAF_CL, ncols * (crank + 1) / TK_LEAF_CL,
-                   wc + ly.part[n] + crank * DD, xd[n], tile);
+      gram(X, xd[n], prod64(xd, n + 1, p), ncols * crank / TK_LEAF_CL, ncols * (crank + 1) / TK_LEAF_CL,
+           wc + ly.part[n] + crank * DD, xd[n]);
     }
     cluster_barrier();
     for (int n = 1; n < p; ++n) {
@@ -515,7 +559,7 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
         if (crank == 0) {
           const S* Y = wc + ly.Y;
           S* A = eig_A(dn, rl[n]);
-          gram_cols<S>(Y, dn, Rn, 0, Rn, A, dn, tile);
+          gram(Y, dn, Rn, 0, Rn, A, dn);
           if (uses_trd(dn, rl[n])) {
             trd_eig<BG, S>(dn, rl[n], A, dn, wc + ly.U[n], rl[n], wt + ly.trd, sm.sc, sm.cl);
           } else {
@@ -586,22 +630,35 @@ __global__ void __cluster_dims__(TK_LEAF_CL, 1, 1) __launch_bounds__(TK_NT)
     }
     cluster_barrier();  // the cluster's workspace is reused by the next job
   }
+  if (tc_on) {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0) tmem_free(st.tmem, kTcTmemCols);
+  }
 }
 
 }  // namespace tk
 
 using namespace tk;
 
-size_t tk_leaf_smem_bytes(int dtype, int nsa, int nsv, int neig, int rmax) {
+size_t tk_leaf_smem_bytes(int dtype, int nsa, int nsv, int neig, int rmax, int64_t tc_bytes) {
   const size_t es = dtype == TK_F64 ? 8 : 4;
   const int half_cap = nsv / 2 + 2;
   size_t b = kHdr + align16(half_cap * sizeof(int));
   b += align16(es * (2 * half_cap + nsv + 2));
   b += align16(es * (size_t)nsa * nsa) + align16(es * (size_t)nsv * nsv);
-  b += align16(es * (size_t)kKC * (((neig + 3) & ~3) + 4));
-  b += align16(es * (size_t)kStage);
-  b += es * (size_t)neig * ((rmax + 3) & ~3);
-  return b;
+  size_t c = align16(es * (size_t)kKC * (((neig + 3) & ~3) + 4));
+  c += align16(es * (size_t)kStage);
+  c += es * (size_t)neig * ((rmax + 3) & ~3);
+  return b + std::max<size_t>(c, (size_t)tc_bytes);
+}
+
+// Bytes of the contraction buffers (tile, stage, us) of the leaf kernel.
+size_t tk_leaf_contraction_bytes(int dtype, int neig, int rmax) {
+  const size_t es = dtype == TK_F64 ? 8 : 4;
+  return align16(es * (size_t)kKC * (((neig + 3) & ~3) + 4)) + align16(es * (size_t)kStage) +
+         es * (size_t)neig * ((rmax + 3) & ~3);
 }
 
 template <class S> static const void* leaf_fn() { return (const void*)k_leaf<S>; }
@@ -625,7 +682,7 @@ int tk_launch_leaf(int dtype, const TkTreeView& tv, const void* raw, int64_t blo
                    int njobs, int ell, const TkWorkspace& ws, const TkLeafLayout& ly, int nclusters,
                    cudaStream_t stream) {
   if (njobs <= 0) return TK_OK;
-  const size_t smem = tk_leaf_smem_bytes(dtype, ly.nsa, ly.nsv, ly.neig, ly.rmax);
+  const size_t smem = tk_leaf_smem_bytes(dtype, ly.nsa, ly.nsv, ly.neig, ly.rmax, ly.tc_bytes);
   const dim3 grid(TK_LEAF_CL * nclusters);
   if (dtype == TK_F64) {
     if (cudaFuncSetAttribute(leaf_fn<double>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

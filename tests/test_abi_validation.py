@@ -43,9 +43,10 @@ def test_defaults_follow_the_paper(lib):
     assert lib.tk_config_default(None) == ARG
 
 
-@pytest.mark.parametrize("bad", [dict(p=1), dict(p=7), dict(leaf_slices=0), dict(theta_num=8, theta_den=7),
+@pytest.mark.parametrize("bad", [dict(p=1), dict(p=9), dict(leaf_slices=0), dict(theta_num=8, theta_den=7),
                                  dict(theta_den=0), dict(theta_num=0), dict(max_iter=0), dict(dtype=5),
-                                 dict(ranks0=0), dict(ranks0=5000), dict(dims1=0), dict(hbm_budget=-1)])
+                                 dict(ranks0=0), dict(ranks0=5000), dict(dims1=0), dict(hbm_budget=-1),
+                                 dict(math=-1), dict(math=3), dict(math=2, dtype=0)])
 def test_invalid_configurations_are_rejected(lib, bad):
     c = _cfg(lib, **bad)
     h = ctypes.c_void_p(1234)
