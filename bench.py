@@ -280,6 +280,16 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json),
+    else the recipe's earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def fp32_alu_peak(tk, dev_index, sm_max_mhz):
     """FP32 CUDA-core peak from unit counts and the maximum clock, and the
     FMA rate the device sustains (tk_probe_fma_rate, CUDA events)."""
@@ -329,6 +339,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched_r16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="answer only the workload's first N queries per step (0: all; for profiling runs)")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="timed launches of the FP32 plain workload's 1000-query batch (0: skip)")
     ap.add_argument("--appends", type=int, default=256,
@@ -339,6 +351,8 @@ def main():
                     help="run only the query-latency-versus-timespan series and print it")
     ap.add_argument("--appends-only", action="store_true",
                     help="run only the append-latency section and print it")
+    ap.add_argument("--p-sweep", action="store_true",
+                    help="run only the sweep over the number of modes (p = 3..7) and print it")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the serving run (appends at 1 kHz; 15.36 s covers T 1024 -> 16384)")
     args = ap.parse_args()
@@ -357,6 +371,10 @@ def main():
     if args.latency_vs_T:
         torch.cuda.set_device(0)
         print(json.dumps({"latency_vs_T": latency_vs_T_section(tk, torch, torch.device("cuda", 0), 0)}))
+        return 0
+    if args.p_sweep:
+        torch.cuda.set_device(0)
+        print(json.dumps({"p_sweep": p_sweep_section(tk, torch, torch.device("cuda", 0), 0)}))
         return 0
     if args.appends_only:
         torch.cuda.set_device(0)
@@ -377,6 +395,8 @@ def main():
     name = args.workload
     w, X = series_of(name)
     Q = synth.query_ranges(w["T"], w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
+    if args.queries > 0:
+        Q = np.ascontiguousarray(Q[: args.queries])
     stream = torch.cuda.Stream(device=dev)
     tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32",
                    device=local, stream=stream)
@@ -481,7 +501,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(w, name), "queries_per_step": n_q,
+        "config": {"workload": workload_desc(w, name) + (f" (first {n_q} queries)" if args.queries else ""),
+                   "queries_per_step": n_q,
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "tree_arena_bytes": tree.arena_bytes()},
@@ -497,7 +518,8 @@ def main():
         "gpu_launches": gpu_launches,
         "roofline": roofline,
         "tree_build": {"seconds": build_s, "raw_bytes": raw_bytes, "roofline": {
-            "bound": "hbm", "achieved": raw_bytes / build_s / 1e9, "unit": "GB/s",
+            "bound": "hbm", "achieved": raw_bytes / build_s / 1e9, "peak": hbm_peak_gbs(), "unit": "GB/s",
+            "frac": raw_bytes / build_s / 1e9 / hbm_peak_gbs(),
             "note": "raw series read once by the leaf kernel; leaves and merges are latency-bound, "
                     "so this is far below the HBM peak"}},
         "clocks": clocks,
@@ -619,6 +641,67 @@ def theta_sweep(tk, torch, dev, local, thetas=((1, 2), (7, 10), (9, 10))):
     return rows
 
 
+P_SWEEP_SHAPES = [(1000, 1000), (100, 100, 100), (100, 100, 10, 10), (100, 10, 10, 10, 10), (10,) * 6]
+
+
+def p_sweep_section(tk, torch, dev, local, lengths=(98, 192, 384), n_q=40, r=5, regime=100, sigma=0.05):
+    """Scalability in the number of modes (the paper's synthetic series of
+    1000 slices and 10^9 entries for p = 3..7, target rank 5, query lengths
+    98, 192 and 384): per p, the tree build time (single-slice leaves, as in
+    the paper) and the p50/p99 latency of n_q queries per length, one query
+    per launch.  The series is piecewise Tucker of rank 5 per regime of 100
+    slices with unit signal RMS and N(0, sigma^2) noise, drawn on the GPU from
+    a seeded generator."""
+    rows = []
+    T = 1000
+    for dims in P_SWEEP_SHAPES:
+        p = len(dims) + 1
+        g = torch.Generator(device=dev)
+        g.manual_seed(3000 + p)
+        X = torch.empty((T,) + dims, dtype=torch.float32, device=dev)
+        for t0 in range(0, T, regime):
+            l = min(regime, T - t0)
+            Y = torch.randn((r,) * p, generator=g, device=dev)
+            for n, d in enumerate((l,) + dims):
+                U, _ = torch.linalg.qr(torch.randn(d, r, generator=g, device=dev))
+                Y = torch.tensordot(U, Y, dims=([1], [n])).movedim(0, n)
+            Y *= (l * float(np.prod(dims))) ** 0.5 / float(Y.norm())  # unit RMS per entry
+            X[t0:t0 + l] = Y + sigma * torch.randn(Y.shape, generator=g, device=dev)
+            del Y
+        stream = torch.cuda.Stream(device=dev)
+        tree = tk.Tree(dims, (r,) * p, leaf_slices=1, max_iter=20, tol=0.01, dtype="f32", device=local,
+                       stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree.build(X)
+        tree.sync()
+        build_s = time.perf_counter() - t0
+        del X
+        torch.cuda.empty_cache()
+        rng = np.random.default_rng(4000 + p)
+        lat = {}
+        for L in lengths:
+            ms = []
+            for s0 in rng.integers(0, T - L + 1, size=n_q):
+                q = np.array([[s0, s0 + L]], dtype=np.int64)
+                o = tree.layout(q)
+                rd, od = torch.from_numpy(q).to(dev), torch.from_numpy(o).to(dev)
+                out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tree.query_batch(rd, od, out)
+                b.record(stream)
+                tree.sync()
+                ms.append(a.elapsed_time(b))
+            lat[str(L)] = {"p50_ms": pct(ms, 50), "p99_ms": pct(ms, 99)}
+        rows.append({"p": p, "shape": [T] + list(dims), "tree_build_s": build_s, "arena_bytes": tree.arena_bytes(),
+                     "latency": lat})
+        tree.close()
+        torch.cuda.empty_cache()
+    return {"workload": f"1000 x ... (10^9 entries), rank {r}, regime {regime}, sigma {sigma}, leaves of one slice, "
+                        f"FP32, tol 0.01; {n_q} queries per length, one per launch", "points": rows}
+
+
 def replica_throughput(local_ms, local_units, world, dist=None, device=None):
     """Whole-job throughput of N replicas (Section 7's queries are
     independent: every rank answers its own copy of the batch, no data-path
@@ -679,6 +762,8 @@ def append_section(tk, torch, dev, local, n_app):
             tail.append(c.elapsed_time(d))
     tree.close()
     q = lambda v, f: sorted(v)[min(len(v) - 1, int(f * len(v)))] if v else None
+    block_bytes = w["B"] * int(np.prod(w["dims"])) * 4
+    mean_done = float(np.mean(done)) if done else None
     return {
         "workload": f"4-way {w['dims'][0]}x{w['dims'][1]}x{w['dims'][2]} slices, ranks {w['ranks']}, leaf {w['B']}, "
                     f"FP32, tol 0.01; tree built to T={T0} ({build_s * 1e3:.1f} ms), then {n_app} appends",
@@ -689,6 +774,13 @@ def append_section(tk, torch, dev, local, n_app):
                               "what": "leaf Tucker-ALS + Stitch of the newly complete ancestors"},
         "open_block_query_ms": {"mean": float(np.mean(tail)) if tail else None, "p99": q(tail, 0.99),
                                 "what": "query over the last 40 slices, decomposing the open block first"},
+        "roofline": {"bound": "hbm", "kernel": "k_leaf<float> + k_stitch merges of one block completion",
+                     "achieved": block_bytes / (mean_done * 1e-3) / 1e9 if mean_done else None,
+                     "peak": hbm_peak_gbs(), "unit": "GB/s",
+                     "frac": block_bytes / (mean_done * 1e-3) / 1e9 / hbm_peak_gbs() if mean_done else None,
+                     "algorithmic_bytes": block_bytes,
+                     "note": "the raw block read once; the decomposition is latency-bound (eigensolvers and "
+                             "barrier-separated steps on 8 SMs), far from this bound"},
     }
 
 
