@@ -353,7 +353,7 @@ def main():
                     help="run only the append-latency section and print it")
     ap.add_argument("--p-sweep", action="store_true",
                     help="run only the sweep over the number of modes (p = 3..7) and print it")
-    ap.add_argument("--serve-seconds", type=float, default=2.0,
+    ap.add_argument("--serve-seconds", type=float, default=15.36,
                     help="length of the serving run (appends at 1 kHz; 15.36 s covers T 1024 -> 16384)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -842,7 +842,11 @@ def serving_section(tk, torch, dev, local, seconds):
     T0 = w["T0"]
     n_app = int(round(seconds * w["append_hz"]))
     T_end = T0 + n_app
-    X = synth.piecewise_tucker_regimes(T_end, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    # slice t of the stream is slice t mod 4096 of the seeded series (whole
+    # regimes of 512, so the regime structure is kept; 16384 distinct slices
+    # of 64x64x32 would be 8.6 GB to generate)
+    POOL = 4096
+    X = synth.piecewise_tucker_regimes(min(T_end, POOL), w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
     tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local)
     tree.build(torch.from_numpy(X[:T0]).to(dev))
     tree.sync()
@@ -868,7 +872,7 @@ def serving_section(tk, torch, dev, local, seconds):
         while time.perf_counter() - t0 < t_ev:
             pass
         if kind == 1:
-            srv.submit_append(X[T_sub])
+            srv.submit_append(X[T_sub % POOL])
             T_sub += 1
             continue
         Lq = int(round(np.exp(np.log(w["lo"]) + u[i, 0] * (np.log(T_sub) - np.log(w["lo"])))))
@@ -909,8 +913,9 @@ def serving_section(tk, torch, dev, local, seconds):
     tree.close()
     return {
         "workload": f"4-way {dims[0]}x{dims[1]}x{dims[2]}xT, T {T0}->{T_end} by appends at "
-                    f"{w['append_hz']:.0f} Hz, Poisson queries at {w['query_hz']:.0f}/s of log-uniform length "
-                    f"{w['lo']}..T, ranks {rk}, leaf {w['B']}, FP32, tol 0.01",
+                    f"{w['append_hz']:.0f} Hz (slice t = slice t mod {POOL} of the seeded series), Poisson queries "
+                    f"at {w['query_hz']:.0f}/s of log-uniform length {w['lo']}..T, ranks {rk}, leaf {w['B']}, FP32, "
+                    "tol 0.01",
         "seconds": seconds, "queries": int(st_load["queries_done"]), "appends": int(st_load["appends_done"]),
         "offered_qps": len(qt) / seconds, "served_qps": st_load["queries_done"] / st_load["elapsed_s"],
         "latency_ms": {"p50": st_load["latency_p50_ms"], "p99": st_load["latency_p99_ms"],

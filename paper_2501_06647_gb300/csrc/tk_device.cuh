@@ -430,203 +430,6 @@ __device__ void householder_apply_q(const S* A, int m, int kmax, int lda, const 
   }
 }
 
-// ---- Tall-skinny Householder QR by warps (TSQR) ---------------------------
-// For the temporal slice of a partial hit (Eq. (partial-tucker)): a tall m x q
-// matrix A (row-major, lda), q <= 32.  The rows are cut into blocks of 32;
-// warp w reduces its own contiguous run of blocks with a running triangle R_w
-// (each step is the Householder QR of [R_w; block], whose reflectors are zero
-// on R_w's rows other than the pivot, so that they are kept in the block's
-// place and R_w stays upper triangular), then the warps' triangles are merged
-// pairwise in a tree of the same steps (Golub & Van Loan, Section 5.2; the
-// "TS" form of Demmel, Grigori, Hoemmen and Langou, 2012).  Data moves once
-// through registers (lane c holds column c) and every reduction is lane-local,
-// so there is no group barrier inside a step.  The product of the
-// reflectors is an orthogonal Q with A = Q [R; 0], R the final triangle.
-//
-// Scratch of one factorization (tsqr_elems): block taus (nblk x q), the merge
-// tree's reflectors ((nw - 1) x q x q) and taus ((nw - 1) x q).  Shared by all
-// factorizations of a group (tsqr_work_elems): nw x 32 q for the warps'
-// triangles (factor) or their q x 32 coefficient blocks (apply), then per warp
-// a 32 x q block buffer, a 32 x 32 buffer of output rows and 40 elements for
-// the current reflector.  Needs 2 <= q <= 32.
-__host__ __device__ inline int64_t tsqr_elems(int64_t m, int q, int nw) {
-  return ((m + 31) / 32) * q + (int64_t)(nw - 1) * q * q + (int64_t)(nw - 1) * q;
-}
-__host__ __device__ inline int64_t tsqr_work_elems(int q, int nw) {
-  return (int64_t)nw * (32 * q + 32 * q + 32 * 32 + 40);
-}
-
-// One structured step by one warp: [Rt (q x q, row-major, ldr); X] = H [R'; 0]
-// with X the 32 x q block in Xb (row-major, ldx).  On return Xb holds the
-// reflectors' lower parts (column j: reflector j), Rt is updated and the taus
-// are in tau[0..q).  Lane c works on column c; vb: 33 elements of
-// warp-private scratch (the current reflector and its tau).
-template <class S>
-__device__ void tsqr_step(S* Rt, int ldr, S* Xb, int ldx, int q, S* tau, S* vb) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < q; ++j) {
-    if (lane == j) {
-      S s = 0;
-      for (int i = 0; i < 32; ++i) {
-        const S x = Xb[i * ldx + j];
-        s += x * x;
-      }
-      const S alpha = Rt[j * ldr + j];
-      S t = 0, beta = alpha, scale = 0;
-      if (s != S(0)) {
-        const S nrm = sqrt(alpha * alpha + s);
-        beta = alpha >= S(0) ? -nrm : nrm;
-        t = (beta - alpha) / beta;
-        scale = S(1) / (alpha - beta);
-      }
-      for (int i = 0; i < 32; ++i) {
-        const S v = Xb[i * ldx + j] * scale;
-        Xb[i * ldx + j] = v;
-        vb[i] = v;
-      }
-      Rt[j * ldr + j] = beta;
-      tau[j] = t;
-      vb[32] = t;
-    }
-    __syncwarp();
-    const S t = vb[32];
-    if (lane > j && lane < q && t != S(0)) {
-      S w = Rt[j * ldr + lane];
-      for (int i = 0; i < 32; ++i) w += vb[i] * Xb[i * ldx + lane];
-      w *= t;
-      Rt[j * ldr + lane] -= w;
-      for (int i = 0; i < 32; ++i) Xb[i * ldx + lane] -= w * vb[i];
-    }
-    __syncwarp();
-  }
-}
-
-// Apply one structured step's reflectors in reverse to [Zt (q x nc, ldz); 0
-// (32 x nc)], the lower part going to Yb (32 x nc, row-major, ldy): lane c
-// (< nc) works on column c.  V (32 x q, row-major, ldv) holds the reflectors'
-// lower parts, tau their taus.
-template <class S>
-__device__ void tsqr_unstep(S* Zt, int ldz, S* Yb, int ldy, int q, int nc, const S* V, int ldv, const S* tau) {
-  const int lane = threadIdx.x & 31;
-  if (lane < nc)
-    for (int i = 0; i < 32; ++i) Yb[i * ldy + lane] = S(0);
-  __syncwarp();
-  if (lane < nc) {
-    for (int j = q - 1; j >= 0; --j) {
-      const S t = tau[j];
-      if (t == S(0)) continue;
-      S w = Zt[j * ldz + lane];
-      for (int i = 0; i < 32; ++i) w += V[i * ldv + j] * Yb[i * ldy + lane];
-      w *= t;
-      Zt[j * ldz + lane] -= w;
-      for (int i = 0; i < 32; ++i) Yb[i * ldy + lane] -= w * V[i * ldv + j];
-    }
-  }
-  __syncwarp();
-}
-
-// Factor A (m x q, lda; m >= q) in place: A's blocks then hold their
-// reflectors, fac the rest (tsqr_elems), R (q x q, row-major, ldr) the
-// triangle.  work: tsqr_work_elems(q, nw).  Executed by group G.
-template <class G, class S>
-__device__ void tsqr_factor(S* A, int64_t m, int q, int lda, S* fac, S* work, S* R, int ldr) {
-  const int tid = G::rank(), lane = tid & 31, warp = tid >> 5, nw = G::nwarps();
-  const int64_t nblk = (m + 31) / 32;
-  S* taub = fac;
-  S* tv = fac + nblk * q;
-  S* tt = tv + (int64_t)(nw - 1) * q * q;
-  S* Rw = work;
-  S* per = work + (int64_t)nw * 32 * q + (int64_t)warp * (32 * q + 32 * 32 + 40);
-  S* Xb = per;                       // 32 x q
-  S* vb = per + 32 * q + 32 * 32;    // 33
-  S* Rme = Rw + (int64_t)warp * q * q;
-  for (int e = lane; e < q * q; e += 32) Rme[e] = S(0);
-  __syncwarp();
-  const int64_t b0 = nblk * warp / nw, b1 = nblk * (warp + 1) / nw;
-  for (int64_t b = b0; b < b1; ++b) {
-    const int64_t r0 = 32 * b;
-    const int mb = (int)((m - r0) < 32 ? (m - r0) : 32);
-    for (int e = lane; e < 32 * q; e += 32) {
-      const int i = e / q, c = e - (e / q) * q;
-      Xb[e] = i < mb ? A[(r0 + i) * lda + c] : S(0);
-    }
-    __syncwarp();
-    tsqr_step<S>(Rme, q, Xb, q, q, taub + b * q, vb);
-    for (int e = lane; e < mb * q; e += 32) {
-      const int i = e / q, c = e - (e / q) * q;
-      A[(r0 + i) * lda + c] = Xb[e];
-    }
-    __syncwarp();
-  }
-  G::sync();
-  // merge tree: warp w absorbs warp w + l at level l (lowest set bit of w + l)
-  for (int l = 1; l < nw; l <<= 1) {
-    if ((warp & (2 * l - 1)) == 0 && warp + l < nw) {
-      const S* Rb = Rw + (int64_t)(warp + l) * q * q;
-      for (int e = lane; e < 32 * q; e += 32) Xb[e] = e < q * q ? Rb[e] : S(0);
-      __syncwarp();
-      tsqr_step<S>(Rme, q, Xb, q, q, tt + (int64_t)(warp + l - 1) * q, vb);
-      S* slot = tv + (int64_t)(warp + l - 1) * q * q;
-      for (int e = lane; e < q * q; e += 32) slot[e] = Xb[e];
-      __syncwarp();
-    }
-    G::sync();
-  }
-  for (int e = tid; e < q * q; e += G::size()) R[(e / q) * ldr + e % q] = Rw[e];
-  G::sync();
-}
-
-// Y (m x nc, ldy) = Q [C; 0] for the Q of tsqr_factor (A and fac as it left
-// them), C (q x nc, row-major, ldc), nc <= 32.  work: tsqr_work_elems(q, nw).
-template <class G, class S>
-__device__ void tsqr_apply(const S* A, int64_t m, int q, int lda, const S* fac, const S* C, int ldc, int nc, S* Y,
-                           int64_t ldy, S* work) {
-  const int tid = G::rank(), lane = tid & 31, warp = tid >> 5, nw = G::nwarps();
-  const int64_t nblk = (m + 31) / 32;
-  const S* taub = fac;
-  const S* tv = fac + nblk * q;
-  const S* tt = tv + (int64_t)(nw - 1) * q * q;
-  S* Z = work;  // nw blocks of q x 32 (leading dimension 32)
-  S* per = work + (int64_t)nw * 32 * q + (int64_t)warp * (32 * q + 32 * 32 + 40);
-  S* Vs = per;                  // 32 x q: a block's reflectors
-  S* Yb = per + 32 * q;         // 32 x 32: its output rows
-  S* Zme = Z + (int64_t)warp * q * 32;
-  if (warp == 0)
-    for (int e = lane; e < q * 32; e += 32) Zme[e] = (e % 32) < nc ? C[(e / 32) * ldc + e % 32] : S(0);
-  G::sync();
-  int top = 1;
-  while (top < nw) top <<= 1;
-  for (int l = top >> 1; l >= 1; l >>= 1) {
-    if ((warp & (2 * l - 1)) == 0 && warp + l < nw) {
-      const S* slot = tv + (int64_t)(warp + l - 1) * q * q;
-      for (int e = lane; e < 32 * q; e += 32) Vs[e] = e < q * q ? slot[e] : S(0);
-      __syncwarp();
-      S* Zb = Z + (int64_t)(warp + l) * q * 32;
-      tsqr_unstep<S>(Zme, 32, Yb, 32, q, nc, Vs, q, tt + (int64_t)(warp + l - 1) * q);
-      for (int e = lane; e < q * 32; e += 32) Zb[e] = (e % 32) < nc ? Yb[e] : S(0);
-      __syncwarp();
-    }
-    G::sync();
-  }
-  const int64_t b0 = nblk * warp / nw, b1 = nblk * (warp + 1) / nw;
-  for (int64_t b = b1 - 1; b >= b0; --b) {
-    const int64_t r0 = 32 * b;
-    const int mb = (int)((m - r0) < 32 ? (m - r0) : 32);
-    for (int e = lane; e < 32 * q; e += 32) {
-      const int i = e / q, j = e - (e / q) * q;
-      Vs[e] = i < mb ? A[(r0 + i) * lda + j] : S(0);
-    }
-    __syncwarp();
-    tsqr_unstep<S>(Zme, 32, Yb, 32, q, nc, Vs, q, taub + b * q);
-    for (int e = lane; e < mb * nc; e += 32) {
-      const int i = e / nc, c = e - (e / nc) * nc;
-      Y[(r0 + i) * ldy + c] = Yb[i * 32 + c];
-    }
-    __syncwarp();
-  }
-  G::sync();
-}
-
 // Scratch of jacobi_eig for order n: the round-robin schedule and rotations.
 template <class S> struct JacobiScratch {
   int* pq;    // >= n/2 + 1

@@ -283,10 +283,7 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   const int64_t Tcap = t->nbcap * t->cfg.leaf_slices;
   int64_t tot = ((int64_t)TK_MAXH * TK_HITREC_BYTES + (int64_t)t->es - 1) / (int64_t)t->es;
   tot += hmax * round32(rprod);
-  // at most two partial hits: the slice and its QR's scratch (TSQR by up to
-  // 32 warps, or Householder taus), and the TSQR work area
-  tot += 2 * (round32(Tcap * r[0]) + round32(std::max<int64_t>(r[0], tk::tsqr_elems(Tcap, r[0], 32))));
-  tot += round32(tk::tsqr_work_elems(r[0], 32));
+  tot += 2 * (round32(Tcap * r[0]) + round32(r[0]));  // at most two partial hits
   int64_t k[TK_MAXP], c[TK_MAXP];
   int64_t neig = (int64_t)hmax * r[0];
   k[0] = c[0] = (int64_t)hmax * r[0];

@@ -60,7 +60,7 @@ template <class S> struct StitchCtx {
   int qmax[TK_MAXP];
   HitRec* hits;       // the job's hit records (shared-memory copy when it fits)
   S *phi[TK_MAXP], *tau[TK_MAXP], *R[TK_MAXP], *E[TK_MAXP], *Vs[TK_MAXP];
-  S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs, *trdv, *tsw;
+  S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs, *trdv;
   int* pq;
   int neig;           // largest eig order of the job
   int smem_used;      // bytes of the shared arena in use
@@ -186,12 +186,6 @@ __device__ inline int recall_count(const TkTreeView& tv, const TkEpoch& ep, int6
 }
 
 __device__ inline void set_err(int* status, int code) { atomicCAS(status, 0, code); }
-
-// A partial hit's slice is factored by TSQR (tsqr_factor) when it is tall:
-// at least 64 rows, 2..32 columns, and at most 32 output columns of U^(1).
-__host__ __device__ inline bool tall_slice(int64_t ell, int nr0, int ro0) {
-  return ell >= 64 && nr0 >= 2 && nr0 <= 32 && ro0 <= 32;
-}
 
 // The GPU's global nanosecond timer (the same clock on every SM).
 __device__ __forceinline__ int64_t global_ns() {
@@ -400,20 +394,15 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       cx.phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
       cx.tau[n] = take(cx.k[n]);
     }
-    bool any_ts = false;
     for (int i = 0; i < cx.nh; ++i) {
       HitRec& h = cx.hits[i];
       if (h.partial) {
-        const int64_t ell = h.hi - h.lo;
-        h.slice = take(ell * (int64_t)h.nr0);
-        const bool ts = tall_slice(ell, h.nr0, cx.ro[0]);
-        any_ts = any_ts || ts;
-        h.stau = take(ts ? tsqr_elems(ell, h.nr0, G::nwarps()) : h.nr0);
+        h.slice = take((h.hi - h.lo) * (int64_t)h.nr0);
+        h.stau = take(h.nr0);
       } else {
         h.slice = h.stau = nullptr;
       }
     }
-    cx.tsw = any_ts ? take(tsqr_work_elems(tv.r[0], G::nwarps())) : nullptr;
     cx.smem_used = (int)scur;
     if (cur > ws_cap && cx.err == 0) cx.err = TK_DEV_ERR_WORKSPACE;
   }
@@ -508,13 +497,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       }
       G::sync();
       const long long c0 = clock64();
-      const bool ts = tall_slice(ell, nr0, cx.ro[0]);
-      S* Rt = cx.W;
-      if (ts) {  // tall slice: TSQR by warps, R (nr0 x nr0) straight into Rt
-        tsqr_factor<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), cx.tsw, Rt, nr0);
-      } else {
-        householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
-      }
+      householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
       qr_cyc += clock64() - c0;
       int tot = 1;
       for (int n = 0; n < p; ++n) {
@@ -532,12 +515,11 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
         }
         b0[idx] = core[src];
       }
+      S* Rt = cx.W;
       const int q0 = h.q[0];
-      if (!ts) {
-        for (int idx = lane; idx < q0 * nr0; idx += nt) {
-          const int a = idx / nr0, b = idx % nr0;
-          Rt[idx] = (b >= a) ? sl[a * nr0 + b] : S(0);
-        }
+      for (int idx = lane; idx < q0 * nr0; idx += nt) {
+        const int a = idx / nr0, b = idx % nr0;
+        Rt[idx] = (b >= a) ? sl[a * nr0 + b] : S(0);
       }
       G::sync();
       ttm<G, S>(b0, dims, p, 0, Rt, nr0, 1, q0, Hc, false);
@@ -710,10 +692,6 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     if (!h.partial) {
       const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride + h.lo * tv.r[0];
       gemm<G, S>(ell, ro[0], h.q[0], tf, tv.r[0], 1, Ci, ro[0], 1, Y, ld0, 1, false);
-    } else if (tall_slice(ell, h.nr0, ro[0])) {
-      // rows = Q~ [C_i; 0], Q~ the TSQR factor of the slice (q_i0 = nr0 here)
-      tsqr_apply<G, S>(reinterpret_cast<S*>(h.slice), ell, h.nr0, h.nr0, reinterpret_cast<S*>(h.stau), Ci, ro[0],
-                       ro[0], Y, ld0, cx.tsw);
     } else {
       for (int idx = lane; idx < ell * ro[0]; idx += nt) {
         const int t = idx / ro[0], a = idx % ro[0];
