@@ -733,13 +733,16 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
   for (int k = 0; k + 2 < n; ++k) {
     const int m0 = k + 1, len = n - m0;
     if (warp == 0) {
+      // column k below the diagonal, read as row k (A is symmetric): lanes
+      // read consecutive addresses
       S sig = 0;
       for (int i = m0 + 1 + lane; i < n; i += 32) {
-        const S x = A[i * lda + k];
+        const S x = A[k * lda + i];
         sig += x * x;
       }
       sig = warp_sum(sig);
-      const S alpha = A[m0 * lda + k];
+      const S alpha = A[k * lda + m0];
+      __syncwarp();  // every lane has read alpha before row k is overwritten
       S beta = 0, v1 = 1, mu = alpha;
       if (sig > S(0)) {
         mu = sqrt(alpha * alpha + sig);
@@ -747,7 +750,7 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
         beta = S(2) * v1 * v1 / (sig + v1 * v1);
         const S inv = S(1) / v1;
         for (int i = m0 + lane; i < n; i += 32) {
-          const S vi = (i == m0) ? S(1) : A[i * lda + k] * inv;
+          const S vi = (i == m0) ? S(1) : A[k * lda + i] * inv;
           v[i] = vi;
           A[k * lda + i] = vi;  // row k is retired: it keeps the reflector
         }
@@ -770,8 +773,17 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
       while (g < 32 && 2 * g * len <= nt) g *= 2;
       if (g == 1) {
         for (int i = m0 + tid; i < n; i += nt) {
+          // eight loads of A issued before their FMAs (A may be in global memory)
           S acc = 0;
-          for (int j = m0; j < n; ++j) acc += A[j * lda + i] * v[j];
+          int j = m0;
+          for (; j + 8 <= n; j += 8) {
+            S a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = A[(j + u) * lda + i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += a[u] * v[j + u];
+          }
+          for (; j < n; ++j) acc += A[j * lda + i] * v[j];
           pv[i] = beta * acc;
         }
       } else {
