@@ -47,11 +47,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// TF32 value of x (round to nearest, ties away), as an FP32 bit pattern.
+// TF32 value of x (round to nearest, ties away), as an FP32 bit pattern
+// whose 13 low mantissa bits are cleared, so that it is exactly the value
+// the tensor core multiplies and x - to_tf32(x) is the exact remainder.
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float(r & 0xFFFFE000u);
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle, core-matrix columns

@@ -6,11 +6,13 @@ dense contractions are the Gram matrices mat_n(X) mat_n(X)^T of the raw block
 they run on the tensor cores as split-TF32 products (FP32 accuracy), with
 TK_MATH_TF32 as single TF32 products, with TK_MATH_CUDA_CORES on the FP32
 CUDA cores.  Each tree is checked against the FP64 oracle's tree, node by
-node (the stored decomposition's model distance relative to the node's
-norm): the split-TF32 tree must be as close to the oracle as the CUDA-core
-tree (within twice its distance, or 1e-4), the single-TF32 tree within 5e-2,
-and the split-TF32 tree's queries must meet the FP32 parity bar of the other
-tests.  Shapes
+node: the captured energy ||H||^2 of every stored node (well-determined
+even where a node's kept subspace is not, as in near-degenerate spectra)
+must agree with the oracle's within 1e-4 relative for split TF32 and the CUDA
+cores and within 1e-2 for single TF32; the reconstruction error values of
+queries within 1e-3 and 1e-2 of the oracle's (relative to max(e, 0.1)); and
+split-TF32 and CUDA-core queries must meet the FP32 model bar of the other
+parity tests.  Shapes
 cover both staging paths of the tensor-core Gram (columns contiguous in
 memory, and rows of the last mode) and Gram orders of one and two 128-row
 tiles.
@@ -45,8 +47,12 @@ def _engine(X, dims, ranks, B, math):
     return t
 
 
-def _worst_node_distance(o, e):
-    worst = 0.0
+def _node_gaps(o, e):
+    """Worst relative difference of the captured energy ||H||^2 of every
+    stored node from the oracle's (well-determined even where the kept
+    subspace is not: a rotation inside a near-degenerate subspace changes
+    nothing of it), and the worst model distance relative to the node norm."""
+    de = dd = 0.0
     for v in o.nodes():
         if v.kind not in ("L", "M"):
             continue
@@ -54,9 +60,11 @@ def _worst_node_distance(o, e):
         level = w.bit_length() - 1
         H, V, r = e.node_payload(level, v.sigma >> level)
         assert list(H.shape) == list(v.H.shape)
-        d = metrics.model_distance(np.float64(H), [np.float64(x) for x in V], v.H, v.V) / np.linalg.norm(v.H)
-        worst = max(worst, d)
-    return worst
+        ho = float(np.sum(v.H ** 2))
+        de = max(de, abs(float(np.sum(np.float64(H) ** 2)) - ho) / ho)
+        dd = max(dd, metrics.model_distance(np.float64(H), [np.float64(x) for x in V], v.H, v.V)
+                 / np.linalg.norm(v.H))
+    return de, dd
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
@@ -64,24 +72,32 @@ def test_leaf_grams_match_the_oracle(case):
     dims, ranks, B, T = CASES[case]
     X = series(T, dims, ranks, 32, 0.05, 40 + case)
     o = oracle_tree(X, dims, ranks, B, 4, 0.0)
-    worst = {}
+    Q = synth.query_ranges(T, 12, 50 + case)
+    ans = [o.query(int(ts), int(te)) for ts, te in Q]
+    energy, dist, qerr = {}, {}, {}
     for math in ("cuda_cores", "auto", "tf32"):
         e = _engine(X, dims, ranks, B, math)
-        worst[math] = _worst_node_distance(o, e)
-        if math == "auto":
-            for ts, te in synth.query_ranges(T, 12, 50 + case):
-                ro = o.query(int(ts), int(te))
-                Ge, Ue, info = e.query(int(ts), int(te))
-                Xs = X[int(ts):int(te)]
-                dist = metrics.model_distance(np.float64(Ge), [np.float64(u) for u in Ue], ro["G"], ro["U"])
-                assert dist < 1e-3 * np.linalg.norm(Xs), (ts, te, dist)
+        energy[math], dist[math] = _node_gaps(o, e)
+        worst_q = 0.0
+        for (ts, te), ro in zip(Q, ans):
+            Ge, Ue, info = e.query(int(ts), int(te))
+            Xs = X[int(ts):int(te)]
+            ee = metrics.relative_error(Xs, np.float64(Ge), [np.float64(u) for u in Ue])
+            eo = metrics.relative_error(Xs, ro["G"], ro["U"])
+            worst_q = max(worst_q, abs(ee - eo) / max(eo, 0.1))
+            if math != "tf32":
+                d = metrics.model_distance(np.float64(Ge), [np.float64(u) for u in Ue], ro["G"], ro["U"])
+                assert d < 1e-3 * np.linalg.norm(Xs), (math, ts, te, d)
+        qerr[math] = worst_q
         e.close()
-    print(f"{dims}: worst node model distance to the FP64 oracle: " +
-          ", ".join(f"{k} {v:.2e}" for k, v in worst.items()))
-    # split TF32 is as accurate as the FP32 CUDA cores; single TF32 (products
-    # rounded to 11 significant bits) within 5e-2
-    assert worst["auto"] <= max(2.0 * worst["cuda_cores"], 1e-4), worst
-    assert worst["tf32"] < 5e-2, worst
+    print(f"{dims}: node energy vs the FP64 oracle " + ", ".join(f"{k} {v:.1e}" for k, v in energy.items()) +
+          "; query error values " + ", ".join(f"{k} {v:.1e}" for k, v in qerr.items()) +
+          "; node model distance " + ", ".join(f"{k} {v:.1e}" for k, v in dist.items()))
+    # split TF32 keeps FP32 accuracy; single TF32 (products rounded to 11
+    # significant bits) within 1e-2 of the energies and error values
+    for m in ("cuda_cores", "auto"):
+        assert energy[m] < 1e-4 and qerr[m] < 1e-3, (m, energy, qerr)
+    assert energy["tf32"] < 1e-2 and qerr["tf32"] < 1e-2, (energy, qerr)
 
 
 def test_tf32_rejected_for_fp64_trees():

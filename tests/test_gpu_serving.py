@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import synth  # noqa: E402
 from gpu_util import series, engine_tree  # noqa: E402
 from oracle import metrics  # noqa: E402
 
@@ -136,3 +137,28 @@ def test_concurrent_submitters_and_admission_limits():
     small.close()
     tree.close()
     twin.close()
+
+
+def test_wait_times_out_and_the_ticket_stays_collectable():
+    # A wait whose limit runs out returns TK_ERR_TIMEOUT and changes nothing:
+    # the request still completes and is collected by a later wait.  The
+    # server is kept busy by 600 queries in batches of 64 on a rank-16 tree,
+    # so the last one cannot be answered within 0.1 ms of its submission.
+    import paper_2501_06647_gb300 as tk
+    w = synth.WORKLOADS["batched_r16"]
+    T = 512
+    X = synth.piecewise_tucker_regimes(T, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"])
+    tree = engine_tree(X, w["dims"], w["ranks"], w["B"], 20, 0.01, "f32")
+    srv = tk.Server(tree, max_batch=64)
+    Q = synth.query_ranges(T, 600, 77, "loguniform", 64, T)
+    tickets = [srv.submit_query(int(a), int(b)) for a, b in Q]
+    with pytest.raises(tk.TuckerError) as ei:
+        srv.wait(tickets[-1], timeout=1e-4)
+    assert ei.value.code == -9
+    G, U, info = srv.wait(tickets[-1], timeout=120.0)
+    assert U[0].shape[0] == int(Q[-1][1] - Q[-1][0]) and info["iters"] >= 1
+    for k in tickets[:-1]:
+        srv.wait(k, timeout=120.0)
+    assert srv.stats()["queries_done"] == len(Q)
+    srv.close()
+    tree.close()
