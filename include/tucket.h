@@ -117,7 +117,9 @@ typedef struct tk_tree tk_tree;
  * still be set. */
 int tk_config_default(tk_config* cfg);
 
-/* Create an empty tree (T = 0) on cfg->device.  cuda_stream is a
+/* Create an empty stream segment tree (Section 4.2: before the first stream
+ * update there is no node; Algorithm 4 creates the first leaf) with T = 0,
+ * on cfg->device.  cuda_stream is a
  * cudaStream_t to run on, or NULL for a stream the tree creates and owns.
  *
  * Memory budget: with cfg->hbm_budget > 0, every call that would take the
@@ -141,6 +143,8 @@ int tk_tree_build(tk_tree* t, const void* X, int64_t T, int io);
  * complete ancestors are re-decomposed by Stitch of their two children. */
 int tk_stream_append(tk_tree* t, const void* slice, int io);
 
+/* The timespan T of the stream (Section 3: the tensor X has T slices after T
+ * stream updates), i.e. the largest valid t_e of a range query; -1 for NULL. */
 int64_t tk_timespan(const tk_tree* t);
 
 /* Pruned hit set of [t_s, t_e) (Algorithm 1), written to host array out.
