@@ -177,30 +177,22 @@ __device__ void mode_gram(const S* X, const int* d, int p, int n, S* A, int lda,
     while ((a + 1) * (2 * dn - a) / 2 <= idx) ++a;
     int b = idx - a * (2 * dn - a + 1) / 2 + a;
     for (; idx < npairs; idx += nt) {
-      // Consecutive threads take consecutive b, whose rows lie `inner`
-      // elements apart: each thread starts its walk over i at b mod inner, so
-      // that a warp's addresses differ by inner + 1 and spread over the
-      // shared-memory banks instead of hitting one.
-      const int s0 = b % inner;
       S acc = 0;
       for (int o = 0; o < outer; ++o) {
         const S* pa = X + (o * dn + a) * inner;
         const S* pb = X + (o * dn + b) * inner;
-        for (int seg = 0; seg < 2; ++seg) {
-          const int i0 = seg == 0 ? s0 : 0, i1 = seg == 0 ? inner : s0;
-          int i = i0;
-          for (; i + 4 <= i1; i += 4) {
-            S xa[4], xb[4];
+        int i = 0;
+        for (; i + 4 <= inner; i += 4) {
+          S xa[4], xb[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              xa[u] = pa[i + u];
-              xb[u] = pb[i + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc += xa[u] * xb[u];
+          for (int u = 0; u < 4; ++u) {
+            xa[u] = pa[i + u];
+            xb[u] = pb[i + u];
           }
-          for (; i < i1; ++i) acc += pa[i] * pb[i];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc += xa[u] * xb[u];
         }
+        for (; i < inner; ++i) acc += pa[i] * pb[i];
       }
       if (accumulate) {
         A[a * lda + b] += acc;
