@@ -283,7 +283,7 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   const int64_t Tcap = t->nbcap * t->cfg.leaf_slices;
   int64_t tot = ((int64_t)TK_MAXH * TK_HITREC_BYTES + (int64_t)t->es - 1) / (int64_t)t->es;
   tot += hmax * round32(rprod);
-  tot += 2 * (round32(Tcap * r[0]) + round32(r[0]));  // at most two partial hits
+  tot += 2 * (round32(Tcap * (r[0] + 1)) + round32(r[0]));  // at most two partial hits (odd-padded rows)
   int64_t k[TK_MAXP], c[TK_MAXP];
   int64_t neig = (int64_t)hmax * r[0];
   k[0] = c[0] = (int64_t)hmax * r[0];
@@ -291,7 +291,7 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
     const int64_t Dn = t->cfg.dims[n];
     k[n] = (int64_t)hmax * r[n];
     c[n] = std::min<int64_t>(Dn, k[n]);
-    tot += round32(Dn * k[n]) + round32(k[n]) + round32(c[n] * k[n]) + round32(c[n] * r[n]) + round32(c[n] * c[n]);
+    tot += round32(Dn * (k[n] + 1)) + round32(k[n]) + round32(c[n] * k[n]) + round32(c[n] * r[n]) + round32(c[n] * c[n]);
     neig = std::max(neig, c[n]);
   }
   tot += round32(c[0] * r[0]) + round32(c[0] * c[0]);

@@ -38,6 +38,13 @@
 
 namespace tk {
 
+// Leading dimension of the matrices that the Householder steps walk by
+// column (Phi_n, a partial hit's temporal slice, the staged output block):
+// the next odd number, so that the 32 lanes of a warp, reading one column on
+// consecutive rows, fall on 32 different shared-memory banks.  (Ranks are
+// often multiples of 16, which puts a whole column on one or two banks.)
+__device__ __forceinline__ int odd_ld(int k) { return k | 1; }
+
 struct HitRec {
   int level, partial;
   int64_t index, node_lo, node_hi, lo, hi, slot;
@@ -391,13 +398,13 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       cx.Vs[n] = trd ? nullptr : take((int64_t)cx.c[n] * cx.c[n]);
     }
     for (int n = 1; n < p; ++n) {
-      cx.phi[n] = take((int64_t)tv.D[n] * cx.k[n]);
+      cx.phi[n] = take((int64_t)tv.D[n] * odd_ld(cx.k[n]));
       cx.tau[n] = take(cx.k[n]);
     }
     for (int i = 0; i < cx.nh; ++i) {
       HitRec& h = cx.hits[i];
       if (h.partial) {
-        h.slice = take((h.hi - h.lo) * (int64_t)h.nr0);
+        h.slice = take((h.hi - h.lo) * (int64_t)odd_ld(h.nr0));
         h.stau = take(h.nr0);
       } else {
         h.slice = h.stau = nullptr;
@@ -490,14 +497,14 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       const int ell = (int)(h.hi - h.lo);
       const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride;
       S* sl = reinterpret_cast<S*>(h.slice);
-      const int nr0 = h.nr0;
+      const int nr0 = h.nr0, lds = odd_ld(nr0);
       for (int idx = lane; idx < ell * nr0; idx += nt) {
         const int t = idx / nr0, c = idx % nr0;
-        sl[idx] = tf[(h.lo + t) * tv.r[0] + c];
+        sl[t * lds + c] = tf[(h.lo + t) * tv.r[0] + c];
       }
       G::sync();
       const long long c0 = clock64();
-      householder_qr<G, S>(sl, ell, nr0, nr0, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
+      householder_qr<G, S>(sl, ell, nr0, lds, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
       qr_cyc += clock64() - c0;
       int tot = 1;
       for (int n = 0; n < p; ++n) {
@@ -519,7 +526,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       const int q0 = h.q[0];
       for (int idx = lane; idx < q0 * nr0; idx += nt) {
         const int a = idx / nr0, b = idx % nr0;
-        Rt[idx] = (b >= a) ? sl[a * nr0 + b] : S(0);
+        Rt[idx] = (b >= a) ? sl[a * lds + b] : S(0);
       }
       G::sync();
       ttm<G, S>(b0, dims, p, 0, Rt, nr0, 1, q0, Hc, false);
@@ -543,8 +550,8 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   const long long t_hits = clock64();
   // ---- non-temporal bases Phi_n = Q_n R_n, and the implicit HOSVD start ---
   for (int n = 1; n < p; ++n) {
-    const int Dn = tv.D[n], kn = cx.k[n], cn = cx.c[n];
-    S* stg = staging((int64_t)Dn * kn);
+    const int Dn = tv.D[n], kn = cx.k[n], cn = cx.c[n], ldp = odd_ld(kn);
+    S* stg = staging((int64_t)Dn * ldp);
     S* Phi = stg ? stg : cx.phi[n];
     for (int i = 0; i < nh; ++i) {
       const HitRec& h = hits[i];
@@ -552,20 +559,20 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       const int qn = h.q[n], ko = h.koff[n];
       for (int idx = lane; idx < Dn * qn; idx += nt) {
         const int d = idx / qn, c = idx % qn;
-        Phi[d * kn + ko + c] = F[d * tv.r[n] + c];
+        Phi[d * ldp + ko + c] = F[d * tv.r[n] + c];
       }
     }
     G::sync();
     const long long c0 = clock64();
-    householder_qr<G, S>(Phi, Dn, kn, kn, cx.tau[n], sm.sc, sm.red, sm.wbuf);
+    householder_qr<G, S>(Phi, Dn, kn, ldp, cx.tau[n], sm.sc, sm.red, sm.wbuf);
     qr_cyc += clock64() - c0;
     S* R = cx.R[n];
     for (int idx = lane; idx < cn * kn; idx += nt) {
       const int a = idx / kn, b = idx % kn;
-      R[idx] = (b >= a) ? Phi[a * kn + b] : S(0);
+      R[idx] = (b >= a) ? Phi[a * ldp + b] : S(0);
     }
     if (stg) {  // the reflectors are needed again for the output
-      for (int idx = lane; idx < Dn * kn; idx += nt) cx.phi[n][idx] = stg[idx];
+      for (int idx = lane; idx < Dn * ldp; idx += nt) cx.phi[n][idx] = stg[idx];
       G::sync();
     }
     for (int idx = lane; idx < cn * cn; idx += nt) A[idx] = 0;
@@ -698,7 +705,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
         Y[t * ld0 + a] = (t < h.q[0]) ? Ci[t * ro[0] + a] : S(0);
       }
       G::sync();
-      householder_apply_q<G, S>(reinterpret_cast<S*>(h.slice), ell, h.q[0], h.nr0, reinterpret_cast<S*>(h.stau), Y, ro[0],
+      householder_apply_q<G, S>(reinterpret_cast<S*>(h.slice), ell, h.q[0], odd_ld(h.nr0), reinterpret_cast<S*>(h.stau), Y, ro[0],
                                 ld0, sm.wbuf);
     }
     if (ro[0] < rq[0]) {
@@ -712,24 +719,24 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     S* Yout = un_dst[n];
     const int64_t ldo = ldn[n];
     const S* E = cx.E[n];
-    const int kn = cx.k[n];
+    const int kn = cx.k[n], ldp = odd_ld(kn);
     // Q_n [E_n; 0], with Phi_n and the block staged in shared memory when possible
-    S* stg = staging((int64_t)Dn * kn + (int64_t)Dn * ro[n]);
+    S* stg = staging((int64_t)Dn * ldp + (int64_t)Dn * odd_ld(ro[n]));
     const S* Ph = cx.phi[n];
     S* Y = Yout;
     int64_t ld = ldo;
     if (stg) {
-      for (int idx = lane; idx < Dn * kn; idx += nt) stg[idx] = cx.phi[n][idx];
+      for (int idx = lane; idx < Dn * ldp; idx += nt) stg[idx] = cx.phi[n][idx];
       Ph = stg;
-      Y = stg + (int64_t)Dn * kn;
-      ld = ro[n];
+      Y = stg + (int64_t)Dn * ldp;
+      ld = odd_ld(ro[n]);
     }
     for (int idx = lane; idx < Dn * ro[n]; idx += nt) {
       const int d = idx / ro[n], a = idx % ro[n];
       Y[d * ld + a] = d < cn ? E[d * ro[n] + a] : S(0);
     }
     G::sync();
-    householder_apply_q<G, S>(Ph, Dn, cn, kn, cx.tau[n], Y, ro[n], ld, sm.wbuf);
+    householder_apply_q<G, S>(Ph, Dn, cn, ldp, cx.tau[n], Y, ro[n], ld, sm.wbuf);
     if (stg || ro[n] < rq[n]) {
       for (int idx = lane; idx < Dn * rq[n]; idx += nt) {
         const int d = idx / rq[n], a = idx % rq[n];
