@@ -414,6 +414,12 @@ def main():
     out_d = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
+    # the batch launch shape (heavy-query threshold), chosen by the engine's
+    # autotuner on this batch before the warm-up (untimed)
+    default_heavy = tree.heavy_hits
+    tt0 = time.perf_counter()
+    heavy, tune_ms = tree.tune_batch(ranges_d, offsets_d, out_d, reps=1)
+    tune_s = time.perf_counter() - tt0
 
     def step():
         tree.query_batch(ranges_d, offsets_d, out_d)
@@ -505,7 +511,12 @@ def main():
                    "queries_per_step": n_q,
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "tree_arena_bytes": tree.arena_bytes()},
+                   "tree_arena_bytes": tree.arena_bytes(),
+                   "heavy_hits": heavy,
+                   "autotune": {"chosen_heavy_hits": heavy, "default_heavy_hits": default_heavy,
+                                "best_ms": tune_ms, "seconds": tune_s,
+                                "note": "tk_batch_tune: each candidate threshold timed once on this batch "
+                                        "before the warm-up"}},
         "latency_ms": {"p50": pct(done_ms, 50), "p99": pct(done_ms, 99),
                        "mode": "in-batch: batch launch to each query's completion (GPU global timer), "
                                f"{n_q} concurrent queries",
@@ -571,6 +582,7 @@ def plain_section(tk, torch, dev, local, steps):
     od = torch.from_numpy(offsets).to(dev)
     out = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    heavy, _ = tree.tune_batch(rd, od, out, reps=2)
     ms = []
     for k in range(steps + 2):
         with torch.cuda.stream(stream):
@@ -586,6 +598,7 @@ def plain_section(tk, torch, dev, local, steps):
     tree.close()
     qps = len(Q) / (np.mean(ms) / 1e3)
     return {"workload": workload_desc(w, "fp32_plain"), "batch_ms": float(np.mean(ms)), "queries_per_s": qps,
+            "heavy_hits": heavy,
             "plain_latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "queries": len(lat)},
             "plain_queries_per_s": 1e3 / float(np.mean(lat)), "batched_over_plain": qps * float(np.mean(lat)) / 1e3,
             "tree_build_s": build_s}

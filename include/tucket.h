@@ -177,6 +177,33 @@ int tk_batch_layout(const tk_tree* t, int n, const int64_t* ranges_host,
 int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t* offsets,
                          const int32_t* ranks, void* out, tk_query_info* info, int io);
 
+/* Launch shape of tk_range_query_batch (no counterpart in the paper).  Its
+ * persistent kernel runs each query whose hit set has at least `hits` nodes
+ * on a whole 512-thread CTA with both shared-memory arenas, and every other
+ * query on a 256-thread half CTA: a whole CTA shortens one query, halves keep
+ * two queries in flight per SM.  hits = 0 restores the default,
+ * max(3, ceil(55 / largest build rank)); values above the kernel's hit limit
+ * (64) run every query on a half.  Answers do not depend on it beyond
+ * rounding order.  TK_ERR_ARG for a NULL tree or hits < 0.
+ * tk_batch_get_heavy_hits reports the threshold in use. */
+int tk_batch_set_heavy_hits(tk_tree* t, int hits);
+int tk_batch_get_heavy_hits(const tk_tree* t, int* hits);
+
+/* Autotuner of that launch shape (no counterpart in the paper): runs the
+ * batch as tk_range_query_batch with io = TK_IO_DEVICE would (ranges,
+ * offsets, out: device pointers of the tree's GPU; out is overwritten), for
+ * each candidate threshold in {3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32, 65}
+ * once untimed and then `reps` times timed with CUDA events on the tree's
+ * stream, skipping a candidate that selects the same heavy queries as the
+ * previous one; keeps the fastest (best of its reps) with
+ * tk_batch_set_heavy_hits and reports it in *best_hits and its time in
+ * *best_ms (optional; -1 when n = 1, which needs no tuning).  Synchronous.
+ * Errors: TK_ERR_ARG for NULL or host pointers, n < 1 or reps < 1; the
+ * errors of tk_range_query_batch, after which the threshold is left as it
+ * was. */
+int tk_batch_tune(tk_tree* t, int n, const int64_t* ranges_dev, const int64_t* offsets_dev,
+                  const int32_t* ranks, void* out_dev, int reps, int* best_hits, float* best_ms);
+
 /* Copy a stored node's decomposition to host memory, packed like a query
  * output with the build ranks and the node's full time range (for tests).
  * ranks_out (TK_MAX_MODES) receives the node's ranks.  Synchronous. */

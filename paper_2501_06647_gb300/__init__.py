@@ -85,6 +85,11 @@ _SIGS = {
     "tk_arena_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
     "tk_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "tk_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "tk_batch_set_heavy_hits": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "tk_batch_get_heavy_hits": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "tk_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_float)]),
     "tk_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "tk_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "tk_range_query_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -296,6 +301,17 @@ class Tree:
     def arena_bytes(self):
         return int(lib().tk_arena_bytes(self.h))
 
+    @property
+    def heavy_hits(self):
+        """Hit count from which a batched query runs on a whole CTA."""
+        v = ctypes.c_int(0)
+        _check(lib().tk_batch_get_heavy_hits(self.h, ctypes.byref(v)), "tk_batch_get_heavy_hits")
+        return int(v.value)
+
+    @heavy_hits.setter
+    def heavy_hits(self, hits):
+        _check(lib().tk_batch_set_heavy_hits(self.h, int(hits)), "tk_batch_set_heavy_hits")
+
     # ---- queries ---------------------------------------------------------
     def hit_set(self, ts, te):
         """Algorithm 1's hit set as (level, index, node_lo, node_hi, lo, hi, partial) tuples."""
@@ -362,6 +378,17 @@ class Tree:
         ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
         _check(lib().tk_range_query_batch(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), ip,
                                           TK_IO_DEVICE), "tk_range_query_batch")
+
+    def tune_batch(self, ranges, offsets, out, ranks=None, reps=2):
+        """Autotune the batch launch shape on this batch (tk_batch_tune):
+        returns (heavy_hits, best_ms) and keeps that threshold.  Synchronous;
+        overwrites out."""
+        n = self._check_batch_args(ranges, offsets, out)
+        rarr, _ = self._ranks_arg(ranks)
+        best, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+        _check(lib().tk_batch_tune(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), int(reps),
+                                   ctypes.byref(best), ctypes.byref(ms)), "tk_batch_tune")
+        return int(best.value), float(ms.value)
 
     def query_batch_noalloc(self, ranges, offsets, out, ranks=None, info=None):
         """Batched range queries that make no device allocation (device buffers).

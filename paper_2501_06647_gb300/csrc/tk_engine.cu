@@ -61,6 +61,7 @@ struct tk_tree {
   int nsm_stitch = 0, nsa_leaf = 0, nsv_leaf = 0, tc_leaf = 0;
   int64_t tc_bytes_leaf = 0;
   int sm_count = 0;
+  int heavy_set = 0;  // batch heavy-query threshold set by the caller (0: default)
   // staging for host io and batch metadata
   DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
   int64_t launches = 0;
@@ -310,7 +311,7 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   tot += round32(wmax);
   tot += round32(rprod);
   // T of the warm start, and the eig scratch if it spills out of shared memory
-  tot += 3 * round32(neig * neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
+  tot += 3 * round32(neig * neig) + round32(neig) + round32(neig + 2) + round32(2 * (neig / 2 + 2)) + round32(neig / 2 + 2);
   // vectors of the tridiagonal eigensolver (a group has at most 32 warps)
   int rmax = 1;
   for (int n = 0; n < p; ++n) rmax = std::max(rmax, r[n]);
@@ -488,6 +489,7 @@ int ensure_ws_leaf(tk_tree* t, int want_clusters, TkLeafLayout* ly) {
 // orders >= ~55, a threshold measured on the FP32 plain workload); k_batch
 // runs them with a whole CTA.
 int heavy_hits(const tk_tree* t) {
+  if (t->heavy_set > 0) return t->heavy_set;
   int r = 1;
   for (int n = 0; n < t->p; ++n) r = std::max(r, t->cfg.ranks[n]);
   return std::max(3, (55 + r - 1) / r);
@@ -735,6 +737,18 @@ int tk_tree_get_config(const tk_tree* t, tk_config* out) {
 }
 int64_t tk_launch_count(const tk_tree* t) { return t ? t->launches : -1; }
 
+int tk_batch_set_heavy_hits(tk_tree* t, int hits) {
+  if (!t || hits < 0) return TK_ERR_ARG;
+  t->heavy_set = std::min(hits, TK_MAXH + 1);
+  return TK_OK;
+}
+
+int tk_batch_get_heavy_hits(const tk_tree* t, int* hits) {
+  if (!t || !hits) return TK_ERR_ARG;
+  *hits = heavy_hits(t);
+  return TK_OK;
+}
+
 int64_t tk_arena_bytes(const tk_tree* t) {
   if (!t) return -1;
   int64_t b = t->core_pool.bytes + t->tfac.bytes + t->node_ranks.bytes;
@@ -937,6 +951,63 @@ int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t
     rc = tk_sync(t);
     if (rc) return rc;
   }
+  return TK_OK;
+}
+
+int tk_batch_tune(tk_tree* t, int n, const int64_t* ranges, const int64_t* offsets, const int32_t* ranks, void* out,
+                  int reps, int* best_hits, float* best_ms) {
+  if (!t || n < 1 || reps < 1 || !best_hits || !ranges || !offsets || !out) return TK_ERR_ARG;
+  if (!(on_device(ranges, t->dev) && on_device(offsets, t->dev) && on_device(out, t->dev))) return TK_ERR_ARG;
+  DeviceGuard g(t->dev);
+  if (best_ms) *best_ms = -1.f;
+  if (n == 1) {  // a single query runs on one CTA whatever the threshold
+    *best_hits = heavy_hits(t);
+    return TK_OK;
+  }
+  // Candidates in increasing order; one above the kernel's hit limit runs
+  // every query on a half CTA.  A candidate that selects the same heavy head
+  // as the previous one is the same launch and is not timed again.
+  static const int cand[] = {3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32, TK_MAXH + 1};
+  const int saved = t->heavy_set;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_ok(cudaEventCreate(&e0));
+  if (rc == TK_OK) rc = cuda_ok(cudaEventCreate(&e1));
+  int prev_split = -1, best_c = heavy_hits(t);
+  float best = 0.f;
+  bool have = false;
+  for (int ci = 0; rc == TK_OK && ci < (int)(sizeof(cand) / sizeof(cand[0])); ++ci) {
+    t->heavy_set = cand[ci];
+    rc = tk_range_query_batch(t, n, ranges, offsets, ranks, out, nullptr, TK_IO_DEVICE);  // warm-up
+    if (rc == TK_OK) rc = tk_sync(t);
+    int split = 0;
+    if (rc == TK_OK) rc = cuda_ok(cudaMemcpy(&split, t->plan.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (rc || split == prev_split) continue;
+    prev_split = split;
+    float ms = 0.f;
+    for (int r = 0; rc == TK_OK && r < reps; ++r) {
+      rc = cuda_ok(cudaEventRecord(e0, t->stream));
+      if (rc == TK_OK) rc = tk_range_query_batch(t, n, ranges, offsets, ranks, out, nullptr, TK_IO_DEVICE);
+      if (rc == TK_OK) rc = cuda_ok(cudaEventRecord(e1, t->stream));
+      if (rc == TK_OK) rc = tk_sync(t);
+      float m = 0.f;
+      if (rc == TK_OK) rc = cuda_ok(cudaEventElapsedTime(&m, e0, e1));
+      if (rc == TK_OK && (r == 0 || m < ms)) ms = m;
+    }
+    if (rc == TK_OK && (!have || ms < best)) {
+      best = ms;
+      best_c = cand[ci];
+      have = true;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) {
+    t->heavy_set = saved;
+    return rc;
+  }
+  t->heavy_set = best_c;
+  *best_hits = best_c;
+  if (best_ms) *best_ms = best;
   return TK_OK;
 }
 

@@ -67,6 +67,10 @@ def test_null_arguments(lib):
     assert lib.tk_range_query_batch_noalloc(None, 1, None, None, None, None, None) == ARG
     assert lib.tk_batch_layout(None, 1, None, None, None) == ARG
     assert lib.tk_hit_set(None, 0, 1, None, 1, None) == ARG
+    v = ctypes.c_int(-7)
+    assert lib.tk_batch_set_heavy_hits(None, 4) == ARG
+    assert lib.tk_batch_get_heavy_hits(None, ctypes.byref(v)) == ARG and v.value == -7
+    assert lib.tk_batch_tune(None, 2, None, None, None, None, 1, ctypes.byref(v), None) == ARG
     assert lib.tk_timespan(None) < 0 and lib.tk_arena_bytes(None) < 0
     sh = ctypes.c_void_p()
     assert lib.tk_server_create(None, None, ctypes.byref(sh)) == ARG

@@ -30,12 +30,14 @@ from _oracle_pool import oracle_answers  # noqa: E402
 from oracle import metrics  # noqa: E402
 from oracle.tree import StreamSegmentTree  # noqa: E402
 
-def _engine_batch(X, dims, ranks, B, max_iter, tol, dtype, Q):
+def _engine_batch(X, dims, ranks, B, max_iter, tol, dtype, Q, heavy=None):
     import paper_2501_06647_gb300 as tk
     dev = torch.device("cuda", 0)
     t = tk.Tree(dims, ranks, leaf_slices=B, max_iter=max_iter, tol=tol, dtype=dtype)
     t.build(torch.from_numpy(np.ascontiguousarray(X, dtype=np.float64 if dtype == "f64" else np.float32)).to(dev))
     t.sync()
+    if heavy is not None:
+        t.heavy_hits = heavy
     offs = t.layout(Q)
     out = torch.full((int(offs[-1]),), float("nan"), dtype=torch.float64 if dtype == "f64" else torch.float32,
                      device=dev)
@@ -71,6 +73,43 @@ def test_heavy_queries_fp64():
     assert heavy >= 40, heavy
     print(f"heavy: {heavy}/{len(Q)} queries of >= 3 hits; worst rel diff {worst[0]:.1e}, angle {worst[1]:.1e}")
     t.close()
+
+
+def test_heavy_threshold_changes_only_the_launch_shape():
+    """The same FP64 batch with every query of >= 3 hits on a whole CTA (the
+    default for a build rank of 20), with every query on a half CTA, and with
+    every query on a whole CTA: the answers agree to FP64 rounding."""
+    import paper_2501_06647_gb300 as tk
+    dims, ranks, B, T = (24, 22), (20, 8, 8), 4, 256
+    X = synth.piecewise_tucker(T, dims, ranks, T, 0.01, 31)
+    Q = synth.query_ranges(T, 60, 33)
+    answers = []
+    for heavy in (None, 65, 1):
+        t, offs, out, info = _engine_batch(X, dims, ranks, B, 3, 0.0, "f64", Q, heavy)
+        assert t.heavy_hits == (3 if heavy is None else heavy)
+        answers.append([_answer(t, out, offs, info, i, int(te - ts)) for i, (ts, te) in enumerate(Q)])
+        if heavy == 1:
+            t.heavy_hits = 0  # back to the default
+            assert t.heavy_hits == 3
+            with pytest.raises(tk.TuckerError):
+                t.heavy_hits = -1
+        t.close()
+    # the autotuner leaves one of its candidates set and the same answers
+    dev = torch.device("cuda", 0)
+    t, offs, out, info = _engine_batch(X, dims, ranks, B, 3, 0.0, "f64", Q)
+    rd, od = torch.from_numpy(np.ascontiguousarray(Q)).to(dev), torch.from_numpy(offs).to(dev)
+    o2 = torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev)
+    best, ms = t.tune_batch(rd, od, o2, reps=1)
+    assert best in (3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32, 65) and t.heavy_hits == best and ms > 0
+    t.query_batch(rd, od, o2, info=info)
+    answers.append([_answer(t, o2.cpu().numpy(), offs, info, i, int(te - ts)) for i, (ts, te) in enumerate(Q)])
+    t.close()
+    for other in answers[1:]:
+        for i, (ts, te) in enumerate(Q):
+            (Ga, Ua, ra), (Gb, Ub, rb) = answers[0][i], other[i]
+            assert ra == rb
+            rel, dist, ang, ea, eb = compare(X, int(ts), int(te), Gb, Ub, Ga, Ua)
+            assert rel < 1e-9 and ang < 1e-3, (ts, te, rel, ang)
 
 
 def _fp32_bar(X, Q, t, offs, out, info, ans, iters):
