@@ -61,6 +61,7 @@ struct tk_tree {
   int nsm_stitch = 0, nsa_leaf = 0, nsv_leaf = 0, tc_leaf = 0;
   int64_t tc_bytes_leaf = 0;
   int sm_count = 0;
+  int smem_optin = 0;  // shared memory a block may opt in to (bytes)
   int heavy_set = 0;  // batch heavy-query threshold set by the caller (0: default)
   // staging for host io and batch metadata
   DevBuf stage_in, stage_out, stage_meta, stage_info, hit_buf, plan;
@@ -494,8 +495,14 @@ int heavy_hits(const tk_tree* t) {
   for (int n = 0; n < t->p; ++n) r = std::max(r, t->cfg.ranks[n]);
   return std::max(3, (55 + r - 1) / r);
 }
-// Shared arena of one half of a k_batch CTA; a heavy query gets both halves.
-size_t batch_half_arena(const tk_tree* t) { (void)t; return 100 * 1024; }
+// Shared arena of one half of a k_batch CTA (a heavy query gets both
+// halves): all the shared memory a block may take, less the two halves'
+// headers, split in two.
+size_t batch_half_arena(const tk_tree* t) {
+  const size_t total = t->smem_optin > 0 ? (size_t)t->smem_optin : 227 * 1024;
+  const size_t hdrs = tk_batch_smem_bytes(t->cfg.dtype, 0);
+  return ((total - hdrs) / 2) & ~(size_t)127;
+}
 
 TkWorkspace ws_view(const tk_tree* t, bool leaf) {
   TkWorkspace w{};
@@ -689,6 +696,7 @@ int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out) {
   t->es = cfg->dtype == TK_F64 ? 8 : 4;
   DeviceGuard g(t->dev);
   cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount, t->dev);
+  cudaDeviceGetAttribute(&t->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->dev);
   if (cuda_stream) {
     t->stream = (cudaStream_t)cuda_stream;
   } else {

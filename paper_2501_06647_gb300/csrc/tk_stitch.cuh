@@ -353,17 +353,15 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       for (int n = 0; n < p; ++n) rmx = cx.ro[n] > rmx ? cx.ro[n] : rmx;
       cx.trdv = take(trd_scratch_elems(neig, rmx, G::nwarps()));
     }
-    // chain buffers: every intermediate has, per mode, at most max(q_max, ro, nr0) (or c_n) entries
-    int64_t tb = 0;
-    for (int n = 0; n < p; ++n) {
-      int64_t s = 1;
-      for (int m = 0; m < p; ++m) {
-        int e = cx.qmax[m] > cx.ro[m] ? cx.qmax[m] : cx.ro[m];
-        if (m == 0 && tv.r[0] > e) e = tv.r[0];
-        if (m == n && cx.c[m] > e) e = cx.c[m];
-        s *= e;
-      }
-      if (s > tb) tb = s;
+    // chain buffers b0, b1: every intermediate of a hit's chain has, per mode,
+    // at most max(q_max, ro) entries (and the stored temporal rank of a
+    // partial hit in time); the core G (ro_1 x ... x ro_p) lives in b1 between
+    // an iteration's last step and the next iteration's chains
+    int64_t tb = 1;
+    for (int m = 0; m < p; ++m) {
+      int e = cx.qmax[m] > cx.ro[m] ? cx.qmax[m] : cx.ro[m];
+      if (m == 0 && tv.r[0] > e) e = tv.r[0];
+      tb *= e;
     }
     for (int n = 0; n < p; ++n) {  // the init's per-hit Gram and its product with R_n's block
       const int64_t g = (int64_t)cx.qmax[n] * cx.qmax[n], rm = (int64_t)cx.c[n] * cx.qmax[n];
@@ -372,19 +370,26 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     }
     cx.b0 = take(tb);
     cx.b1 = take(tb);
-    cx.N = take(tb);
+    cx.G = cx.b1;
+    // K (k_1 rows of prod_{m>=2} ro_m) is dead once the temporal eigenvectors
+    // C are formed, before any N_n (c_n in mode n, ro elsewhere) is written:
+    // one buffer holds both
     int64_t Kel = cx.k[0];
     for (int m = 1; m < p; ++m) Kel *= cx.ro[m];
+    for (int n = 1; n < p; ++n) {
+      int64_t s = cx.c[n];
+      for (int m = 0; m < p; ++m)
+        if (m != n) s *= cx.ro[m];
+      Kel = s > Kel ? s : Kel;
+    }
     cx.K = take(Kel);
+    cx.N = cx.K;
     int wmax = tv.r[0] * tv.r[0];
     for (int m = 0; m < p; ++m) {
       const int v = cx.ro[m] * (cx.qmax[m] > 1 ? cx.qmax[m] : 1);
       if (v > wmax) wmax = v;
     }
     cx.W = take(wmax);
-    int64_t gel = 1;
-    for (int n = 0; n < p; ++n) gel *= cx.ro[n];
-    cx.G = take(gel);
     for (int n = 0; n < p; ++n) cx.E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
     for (int n = 1; n < p; ++n) cx.R[n] = take((int64_t)cx.c[n] * cx.k[n]);
     for (int i = 0; i < cx.nh; ++i) {
@@ -690,6 +695,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       }
       core_dst[idx] = inside ? Gc[src] : S(0);
     }
+    G::sync();  // G lives in b1, which the staging below may overwrite
   }
   for (int i = 0; i < nh; ++i) {
     const HitRec& h = hits[i];
