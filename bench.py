@@ -341,6 +341,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="answer only the workload's first N queries per step (0: all; for profiling runs)")
+    ap.add_argument("--eig64-steps", type=int, default=2,
+                    help="timed launches of the headline batch with FP64 stitch eigenproblems (0: skip)")
     ap.add_argument("--plain-steps", type=int, default=5,
                     help="timed launches of the FP32 plain workload's 1000-query batch (0: skip)")
     ap.add_argument("--appends", type=int, default=256,
@@ -538,6 +540,8 @@ def main():
 
     del out_d, flush
     torch.cuda.empty_cache()
+    if args.eig64_steps > 0:
+        line["eig_fp64"] = eig64_throughput(tk, torch, dev, local, w, X, Q, args.eig64_steps)
 
     if args.plain_steps > 0:
         line["plain_r10"] = plain_section(tk, torch, dev, local, args.plain_steps)
@@ -701,9 +705,10 @@ def p_sweep_section(tk, torch, dev, local, lengths=(98, 192, 384), n_q=40, r=5, 
                 rd, od = torch.from_numpy(q).to(dev), torch.from_numpy(o).to(dev)
                 out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                tree.query_batch(rd, od, out)
-                b.record(stream)
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    tree.query_batch(rd, od, out)
+                    b.record(stream)
                 tree.sync()
                 ms.append(a.elapsed_time(b))
             lat[str(L)] = {"p50_ms": pct(ms, 50), "p99_ms": pct(ms, 99)}
@@ -759,17 +764,18 @@ def append_section(tk, torch, dev, local, n_app):
 
     app, done, tail = [], [], []
     for k in range(n_app):
-        T = tree.T
-        a = ev()
-        tree.append(Xd[T])
-        b = ev()
-        r = torch.tensor([[max(0, T + 1 - 40), T + 1]], dtype=torch.int64, device=dev)
-        o = torch.from_numpy(tree.layout(r.cpu().numpy())).to(dev)
-        out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
-        c = ev()
-        tree.query_batch(r, o, out)
-        d = ev()
-        tree.sync()
+        with torch.cuda.stream(stream):  # the tree's stream: calls stay asynchronous
+            T = tree.T
+            a = ev()
+            tree.append(Xd[T])
+            b = ev()
+            r = torch.tensor([[max(0, T + 1 - 40), T + 1]], dtype=torch.int64, device=dev)
+            o = torch.from_numpy(tree.layout(r.cpu().numpy())).to(dev)
+            out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
+            c = ev()
+            tree.query_batch(r, o, out)
+            d = ev()
+            tree.sync()
         (done if (T + 1) % w["B"] == 0 else app).append(a.elapsed_time(b))
         if (T + 1) % w["B"] != 0:
             tail.append(c.elapsed_time(d))
@@ -830,9 +836,10 @@ def latency_vs_T_section(tk, torch, dev, local, L=384, n_q=50, checkpoints=(512,
             out = torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            tree.query_batch(rd, od, out)
-            b.record(stream)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                tree.query_batch(rd, od, out)
+                b.record(stream)
             tree.sync()
             ms.append(a.elapsed_time(b))
             hits.append(len(tree.hit_set(int(s0), int(s0 + L))))
@@ -969,7 +976,8 @@ def cpu_section(line, w, X, Q, offsets, tree, out_chk, info):
         eo.append(metrics.relative_error(Xs, res[j][1], res[j][2]))
         dd.append(metrics.model_distance(G, U, res[j][1], res[j][2]) / np.linalg.norm(Xs))
     eg, eo = np.array(eg), np.array(eo)
-    line["accuracy"] = {"queries": len(eg), "mean_rel_err_gpu": float(np.mean(eg)),
+    variants = precision_variants(w, X, Q, sample[:150], res)
+    line["accuracy"] = {"variants": variants,"queries": len(eg), "mean_rel_err_gpu": float(np.mean(eg)),
                         "mean_rel_err_oracle_fp64": float(np.mean(eo)),
                         "mean_rel_err_relative_diff": float(abs(np.mean(eg) - np.mean(eo)) / np.mean(eo)),
                         "max_abs_err_diff": float(np.max(np.abs(eg - eo))),
@@ -977,6 +985,71 @@ def cpu_section(line, w, X, Q, offsets, tree, out_chk, info):
                         "matched_vs_plain": "the batched launch and the one-query-per-launch method run the same "
                                             "kernels on the same tree: identical errors",
                         "note": "both with tol 0.01; iteration counts may differ near the threshold"}
+
+
+def precision_variants(w, X, Q, idx, res):
+    """Error of other arithmetic variants against the FP64 oracle on the same
+    sampled queries: trees over the oracle's prefix of the series (the same
+    nodes and hit sets for these queries) with the stitch eigenproblems in
+    FP64, or the leaf Grams as single TF32 or on FP32 CUDA cores."""
+    import torch
+    import paper_2501_06647_gb300 as tk
+    from oracle import metrics
+    out = {}
+    Qs = np.ascontiguousarray(Q[idx])
+    for name, kw in (("fp32_stitch_fp64_eig", dict(eig_fp64=True)), ("leaf_grams_tf32", dict(math="tf32")),
+                     ("leaf_grams_cuda_cores", dict(math="cuda_cores"))):
+        t = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", **kw)
+        t.build(torch.from_numpy(np.ascontiguousarray(X[:ORACLE_T])).cuda())
+        offs = t.layout(Qs)
+        o, _, info = t.query_batch_host(Qs, offs, None, with_info=True)
+        eg, eo, dd = [], [], []
+        for j, (ts, te) in enumerate(Qs):
+            ts, te = int(ts), int(te)
+            G, U = t.unpack(o[offs[j]:offs[j + 1]], te - ts)
+            r = list(info[j].ranks[: t.p])
+            G = np.float64(G[tuple(slice(0, x) for x in r)])
+            U = [np.float64(u[:, :x]) for u, x in zip(U, r)]
+            Xs = np.asarray(X[ts:te], dtype=np.float64)
+            eg.append(metrics.relative_error(Xs, G, U))
+            eo.append(metrics.relative_error(Xs, res[j][1], res[j][2]))
+            dd.append(metrics.model_distance(G, U, res[j][1], res[j][2]) / np.linalg.norm(Xs))
+        eg, eo = np.array(eg), np.array(eo)
+        out[name] = {"mean_rel_err_relative_diff": float(abs(np.mean(eg) - np.mean(eo)) / np.mean(eo)),
+                     "max_abs_err_diff": float(np.max(np.abs(eg - eo))),
+                     "max_model_distance_rel": float(np.max(dd))}
+        t.close()
+    return out
+
+
+def eig64_throughput(tk, torch, dev, local, w, X, Q, steps):
+    """The headline batch on a tree whose stitch eigenproblems run in FP64
+    (tk_config.eig_fp64), autotuned and timed like the headline."""
+    stream = torch.cuda.Stream(device=dev)
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32",
+                   device=local, stream=stream, eig_fp64=True)
+    tree.build(torch.from_numpy(X).to(dev))
+    tree.sync()
+    offsets = tree.layout(Q)
+    rd = torch.from_numpy(Q.copy()).to(dev)
+    od = torch.from_numpy(offsets).to(dev)
+    out = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    heavy, _ = tree.tune_batch(rd, od, out, reps=1)
+    ms = []
+    for k in range(steps + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.query_batch(rd, od, out)
+            b.record(stream)
+        b.synchronize()
+        if k >= 1:
+            ms.append(a.elapsed_time(b))
+    tree.close()
+    return {"ms_per_step": float(np.mean(ms)), "queries_per_s": len(Q) / (np.mean(ms) / 1e3), "heavy_hits": heavy,
+            "note": "same workload and batch as the headline, stitch eigenproblems (orders >= 20) in FP64"}
 
 
 if __name__ == "__main__":

@@ -63,7 +63,8 @@ typedef enum tk_dtype { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
  *   TK_MATH_CUDA_CORES FP32 (or FP64) CUDA cores;
  *   TK_MATH_TF32       tensor cores with one TF32 product (FP32 accumulation):
  *                      faster, about 1e-3 relative error per product.
- * Everything else (the stitch, eigensolvers, QR) runs in the tree's dtype. */
+ * Everything else (the stitch, eigensolvers, QR) runs in the tree's dtype,
+ * except the stitch eigenproblems under tk_config.eig_fp64. */
 typedef enum tk_math { TK_MATH_AUTO = 0, TK_MATH_CUDA_CORES = 1, TK_MATH_TF32 = 2 } tk_math;
 typedef enum tk_io { TK_IO_DEVICE = 0, TK_IO_HOST = 1 } tk_io;
 
@@ -81,6 +82,11 @@ typedef struct tk_config {
   int32_t device;                   /* CUDA device ordinal */
   int64_t hbm_budget;               /* device bytes the tree may hold (0: no limit) */
   int32_t math;                     /* tk_math of the leaf Grams (TK_MATH_TF32: FP32 trees only) */
+  int32_t eig_fp64;                 /* 1: an FP32 tree solves the eigenproblems of its stitches
+                                       (queries and node merges, Algorithm 2) in FP64 on the GPU,
+                                       for orders >= 20 (the tridiagonal method; smaller orders
+                                       use FP32 Jacobi); 0 (default): in the tree's dtype.  FP64
+                                       trees ignore it.  0 or 1. */
 } tk_config;
 
 /* One node of a hit set (Algorithm 1, Section 5.1), in time order. */
@@ -171,7 +177,11 @@ int tk_range_query(tk_tree* t, int64_t t_s, int64_t t_e, const int32_t* ranks,
  * With io = TK_IO_DEVICE, ranges/offsets/out are device pointers and the
  * call is asynchronous; with TK_IO_HOST they are host pointers and the call
  * copies in, computes, copies out and synchronizes.  info: optional host
- * array of n reports (makes the call synchronous). */
+ * array of n reports (makes the call synchronous).  The launch is ordered on
+ * the tree's stream only: device buffers that work on another stream writes
+ * (a fill of `out`, say) must be complete before the call, or that stream
+ * must be the tree's; a tree created with a NULL stream runs on a stream of
+ * its own that does not synchronize with the legacy default stream. */
 int tk_batch_layout(const tk_tree* t, int n, const int64_t* ranges_host,
                     const int32_t* ranks, int64_t* offsets_host);
 int tk_range_query_batch(tk_tree* t, int n, const int64_t* ranges, const int64_t* offsets,

@@ -33,7 +33,8 @@ class TkConfig(ctypes.Structure):
                 ("ranks", ctypes.c_int32 * MAX_MODES), ("leaf_slices", ctypes.c_int32),
                 ("theta_num", ctypes.c_int32), ("theta_den", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("dtype", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_int64), ("math", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_int64), ("math", ctypes.c_int32),
+                ("eig_fp64", ctypes.c_int32)]
 
 
 class TkHit(ctypes.Structure):
@@ -185,11 +186,12 @@ class Tree:
     leaf_slices the slices per leaf block, theta the pruning threshold as a
     fraction (num, den), dtype "f64" or "f32", hbm_budget the device bytes the
     tree may hold (0: no limit), math the arithmetic of the leaf Grams ("auto":
-    split-TF32 tensor cores for FP32 trees, "cuda_cores", or "tf32").
+    split-TF32 tensor cores for FP32 trees, "cuda_cores", or "tf32"), eig_fp64
+    whether an FP32 tree solves its stitch eigenproblems in FP64.
     """
 
     def __init__(self, dims, ranks, leaf_slices=1, theta=(7, 10), max_iter=20, tol=0.01, dtype="f32",
-                 device=0, stream=None, hbm_budget=0, math="auto"):
+                 device=0, stream=None, hbm_budget=0, math="auto", eig_fp64=False):
         self.dims = tuple(int(d) for d in dims)
         self.ranks = tuple(int(r) for r in ranks)
         self.p = len(self.ranks)
@@ -212,6 +214,7 @@ class Tree:
         cfg.device = int(device)
         cfg.hbm_budget = int(hbm_budget)
         cfg.math = MATH[math]
+        cfg.eig_fp64 = 1 if eig_fp64 else 0
         self.cfg = cfg
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()
@@ -219,6 +222,7 @@ class Tree:
         self.h = h
         self.B = int(leaf_slices)
         self.device = int(device)
+        self._stream = stream
 
     def save(self, path):
         """Write the tree to a file (tk_tree_save; synchronous)."""
@@ -244,6 +248,7 @@ class Tree:
         self.np_dtype = _np_dtype(self.dtype)
         self.B = int(cfg.leaf_slices)
         self.device = int(cfg.device)
+        self._stream = stream
         return self
 
     def close(self):
@@ -265,7 +270,9 @@ class Tree:
             X = np.ascontiguousarray(X, dtype=self.np_dtype)
         else:
             _device_tensor(X, "X", self.device, self._torch_dtype(), (X.shape[0],) + self.dims)
+        f = self._before(io == TK_IO_DEVICE)
         _check(lib().tk_tree_build(self.h, _ptr(X), int(X.shape[0]), io), "tk_tree_build")
+        self._after(f)
 
     def append(self, X_T):
         """stream update with one slice (torch CUDA tensor or host numpy array)."""
@@ -274,7 +281,34 @@ class Tree:
             X_T = np.ascontiguousarray(X_T, dtype=self.np_dtype)
         else:
             _device_tensor(X_T, "X_T", self.device, self._torch_dtype(), self.dims)
+        f = self._before(io == TK_IO_DEVICE)
         _check(lib().tk_stream_append(self.h, _ptr(X_T), io), "tk_stream_append")
+        self._after(f)
+
+    # Stream ordering of device tensors.  The engine launches on the tree's
+    # stream.  When that is torch's current stream, calls are asynchronous and
+    # ordered like torch's own kernels (the caching allocator does not reuse a
+    # freed tensor's memory before the stream reaches that point).  Otherwise
+    # (a tree with a stream of its own, or another current stream) a call
+    # first waits for torch's current stream, so that its inputs are written,
+    # and then for the tree's stream, so that the caller may free or reuse its
+    # tensors as soon as the call returns.
+    def _foreign_stream(self):
+        import torch
+        if self._stream is None:
+            return True
+        return torch.cuda.current_stream(self.device).cuda_stream != self._stream.cuda_stream
+
+    def _before(self, device_io):
+        foreign = device_io and self._foreign_stream()
+        if foreign:
+            import torch
+            torch.cuda.current_stream(self.device).synchronize()
+        return foreign
+
+    def _after(self, foreign):
+        if foreign:
+            self.sync()
 
     def _torch_dtype(self):
         return "float64" if self.dtype == "f64" else "float32"
@@ -371,13 +405,16 @@ class Tree:
 
         ranges: int64 tensor (n, 2); offsets: int64 tensor (n+1); out: tensor
         of offsets[-1] elements of the tree's dtype.  info: optional host
-        array of TkQueryInfo (makes the call synchronous).
+        array of TkQueryInfo (makes the call synchronous).  Asynchronous
+        only when torch's current stream is the tree's (see _foreign_stream).
         """
         n = self._check_batch_args(ranges, offsets, out)
         rarr, _ = self._ranks_arg(ranks)
         ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
+        f = self._before(True)
         _check(lib().tk_range_query_batch(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), ip,
                                           TK_IO_DEVICE), "tk_range_query_batch")
+        self._after(f)
 
     def tune_batch(self, ranges, offsets, out, ranks=None, reps=2):
         """Autotune the batch launch shape on this batch (tk_batch_tune):
@@ -386,6 +423,7 @@ class Tree:
         n = self._check_batch_args(ranges, offsets, out)
         rarr, _ = self._ranks_arg(ranks)
         best, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+        self._before(True)
         _check(lib().tk_batch_tune(self.h, n, _ptr(ranges), _ptr(offsets), rarr, _ptr(out), int(reps),
                                    ctypes.byref(best), ctypes.byref(ms)), "tk_batch_tune")
         return int(best.value), float(ms.value)
@@ -399,8 +437,10 @@ class Tree:
         n = self._check_batch_args(ranges, offsets, out)
         rarr, _ = self._ranks_arg(ranks)
         ip = ctypes.cast(info, ctypes.c_void_p) if info is not None else None
+        f = self._before(True)
         _check(lib().tk_range_query_batch_noalloc(self.h, n, _ptr(ranges), _ptr(offsets),
                                                   rarr, _ptr(out), ip), "tk_range_query_batch_noalloc")
+        self._after(f)
 
     def query_batch_host(self, ranges, offsets=None, out=None, ranks=None, with_info=True):
         """Batched range queries through the C ABI with HOST buffers (copies inside the call)."""

@@ -27,6 +27,7 @@ struct TkTreeView {
   int theta_num, theta_den;
   int max_iter;
   double tol;
+  int eig64;               // FP32 tree: stitch eigenproblems (tridiagonal method) in FP64
   int64_t T, nb, nbt;      // slices, complete blocks, blocks incl. the tail
   int height;              // ceil(log2 nbt) + 1, 0 when empty
   int nlevels;

@@ -68,6 +68,7 @@ template <class S> struct StitchCtx {
   HitRec* hits;       // the job's hit records (shared-memory copy when it fits)
   S *phi[TK_MAXP], *tau[TK_MAXP], *R[TK_MAXP], *E[TK_MAXP], *Vs[TK_MAXP];
   S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs, *trdv;
+  double *Ad, *Ed, *trdd, *scd;  // FP64 eigenproblem of an FP32 tree (eig64)
   int* pq;
   int neig;           // largest eig order of the job
   int smem_used;      // bytes of the shared arena in use
@@ -352,6 +353,13 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       int rmx = 1;
       for (int n = 0; n < p; ++n) rmx = cx.ro[n] > rmx ? cx.ro[n] : rmx;
       cx.trdv = take(trd_scratch_elems(neig, rmx, G::nwarps()));
+      cx.Ad = cx.Ed = cx.trdd = cx.scd = nullptr;
+      if (sizeof(S) == 4 && tv.eig64) {  // take() counts floats: two per double
+        cx.Ad = reinterpret_cast<double*>(take(2 * (int64_t)neig * neig));
+        cx.Ed = reinterpret_cast<double*>(take(2 * (int64_t)neig * rmx));
+        cx.trdd = reinterpret_cast<double*>(take(2 * (int64_t)trd_scratch_elems(neig, rmx, G::nwarps())));
+        cx.scd = reinterpret_cast<double*>(take(16));
+      }
     }
     // chain buffers b0, b1: every intermediate of a hit's chain has, per mode,
     // at most max(q_max, ro) entries (and the stored temporal rank of a
@@ -455,7 +463,15 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   auto eig = [&](int mode_n, int nsz, S* Edst, int lde) {
     const long long c0 = clock64();
     const int rkeep = cx.ro[mode_n];
-    if (nsz >= kTrdMinOrder && rkeep <= kTrdMaxRank) {
+    if (nsz >= kTrdMinOrder && rkeep <= kTrdMaxRank && cx.Ad) {
+      // FP64 under an FP32 stitch: the matrix widened, the eigenproblem
+      // solved in FP64, the eigenvectors rounded to FP32
+      for (int i = lane; i < nsz * nsz; i += nt) cx.Ad[i] = (double)A[i];
+      G::sync();
+      trd_eig<G, double>(nsz, rkeep, cx.Ad, nsz, cx.Ed, rkeep, cx.trdd, cx.scd, sm.cl);
+      for (int i = lane; i < nsz * rkeep; i += nt) Edst[(i / rkeep) * lde + i % rkeep] = (S)cx.Ed[i];
+      G::sync();
+    } else if (nsz >= kTrdMinOrder && rkeep <= kTrdMaxRank) {
       trd_eig<G, S>(nsz, rkeep, A, nsz, Edst, lde, cx.trdv, sm.sc, sm.cl);
     } else {
       S* Vs = cx.Vs[mode_n];

@@ -120,8 +120,9 @@ def test_noalloc_refuses_an_undecomposed_open_block():
 
 def test_noalloc_device_errors_reach_tk_sync():
     # An invalid range inside a device-resident batch is found by the kernel; the
-    # asynchronous call (no report) leaves it in the tree's sticky status word,
-    # which the next tk_sync returns.
+    # call (no report) leaves it in the tree's sticky status word, which the
+    # next tk_sync returns: the binding's own, right after the launch, on a
+    # tree with a stream of its own, else the caller's.
     import paper_2501_06647_gb300 as tk
     dims, ranks = (9, 7), (3, 3, 3)
     X = series(32, dims, ranks, 16, 0.05, 5)
@@ -131,10 +132,10 @@ def test_noalloc_device_errors_reach_tk_sync():
     offs = t.layout(Q)
     r, o = torch.from_numpy(Q).to(dev), torch.from_numpy(offs).to(dev)
     out = torch.zeros(int(offs[-1]), dtype=torch.float64, device=dev)
-    t.query_batch_noalloc(r, o, out)
     with pytest.raises(tk.TuckerError) as ei:
+        t.query_batch_noalloc(r, o, out)
         t.sync()
-    assert ei.value.code == -2
+    assert ei.value.code == -2 and "tk_sync" in str(ei.value)
     t.close()
 
 
