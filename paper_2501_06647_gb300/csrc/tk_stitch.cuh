@@ -54,6 +54,7 @@ struct HitRec {
   void* stau;         // its tau
   int q[TK_MAXP];     // ranks of H~_i
   int nr0;            // stored temporal rank of the node
+  int chol;           // partial hit factored by Cholesky QR (R in the slice buffer), else Householder
   int koff[TK_MAXP];  // column offset of the hit's block in mode n's coefficient space
 };
 static_assert(sizeof(HitRec) <= TK_HITREC_BYTES, "HitRec grew: update TK_HITREC_BYTES");
@@ -490,6 +491,88 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   };
   int dims[TK_MAXP];
 
+  // Cholesky QR of the ell x m slice S (rows ld apart; ell >= 2m): the Gram
+  // S^T S, summed over chunks of rows staged in b0, then its Cholesky factor
+  // R (upper triangular, positive diagonal) by warp 0, so that S = Q R with
+  // Q = S R^{-1}.  Accepted when the diagonal of R spans at most a factor of
+  // 10 (condition number of S near 10 or below: Q is then orthonormal to
+  // about 100 ulps); R goes to Rout (leading dimension ldr, zeros below the
+  // diagonal).  Returns false, on every thread, otherwise: the caller falls
+  // back to Householder.
+  auto cholesky_qr = [&](const S* Sg, int ld, int ell, int m, S* Rout, int ldr) -> bool {
+    const int npair = m * (m + 1) / 2;
+    if (npair > nt) return false;  // one pair of columns per thread
+    S* Gm = cx.b1;  // m x m Gram, then R in its upper triangle
+    S* st = cx.b0;  // staged rows
+    int ch = 0;
+    {
+      int64_t cap = 1;
+      for (int n = 0; n < p; ++n) cap *= (cx.qmax[n] > cx.ro[n] ? cx.qmax[n] : cx.ro[n]);
+      ch = (int)(cap / m);
+      if (ch < 1) ch = 1;
+    }
+    int pa = 0, pb = 0;  // this thread's pair (a <= b) of the packed upper triangle
+    if (lane < npair) {
+      int rem = lane;
+      while (rem >= m - pa) {
+        rem -= m - pa;
+        ++pa;
+      }
+      pb = pa + rem;
+    }
+    S acc0 = 0, acc1 = 0;
+    for (int t0 = 0; t0 < ell; t0 += ch) {
+      const int cn = ell - t0 < ch ? ell - t0 : ch;
+      for (int idx = lane; idx < cn * m; idx += nt) {
+        const int t = idx / m, c = idx - (idx / m) * m;
+        st[idx] = Sg[(int64_t)(t0 + t) * ld + c];
+      }
+      G::sync();
+      if (lane < npair) {
+        int t = 0;
+        for (; t + 1 < cn; t += 2) {
+          acc0 += st[t * m + pa] * st[t * m + pb];
+          acc1 += st[(t + 1) * m + pa] * st[(t + 1) * m + pb];
+        }
+        if (t < cn) acc0 += st[t * m + pa] * st[t * m + pb];
+      }
+      G::sync();
+    }
+    if (lane < npair) Gm[pa * m + pb] = acc0 + acc1;
+    G::sync();
+    if (lane < 32) {
+      int ok = 1;
+      S dmin = 0, dmax = 0;
+      for (int k = 0; k < m; ++k) {
+        S d = Gm[k * m + k];
+        for (int i = 0; i < k; ++i) d -= Gm[i * m + k] * Gm[i * m + k];
+        if (!(d > S(0))) ok = 0;
+        const S rkk = ok ? sqrt(d) : S(1);
+        dmin = k == 0 ? rkk : fmin(dmin, rkk);
+        dmax = k == 0 ? rkk : fmax(dmax, rkk);
+        for (int j = k + 1 + lane; j < m; j += 32) {
+          S v = Gm[k * m + j];
+          for (int i = 0; i < k; ++i) v -= Gm[i * m + k] * Gm[i * m + j];
+          Gm[k * m + j] = v / rkk;
+        }
+        __syncwarp();
+        if (lane == 0) Gm[k * m + k] = rkk;
+        __syncwarp();
+      }
+      if (lane == 0) sm.flag = (ok && dmin * S(10) >= dmax) ? 1 : 0;
+    }
+    G::sync();
+    const bool good = sm.flag != 0;
+    if (good) {
+      for (int idx = lane; idx < m * m; idx += nt) {
+        const int a = idx / m, b = idx - (idx / m) * m;
+        Rout[a * ldr + b] = b >= a ? Gm[a * m + b] : S(0);
+      }
+    }
+    G::sync();
+    return good;
+  };
+
   // ---- hit decompositions: stored payloads or Eq. (partial-tucker) -------
   S hn2 = 0;
   for (int i = 0; i < nh; ++i) {
@@ -514,18 +597,23 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       }
       G::sync();
     } else {
-      // slice rows of the node's temporal factor, QR, then H x_1 R~
+      // slice S (ell x nr0) of the node's temporal factor, S = Q R~, then H x_1 R~
       const int ell = (int)(h.hi - h.lo);
       const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride;
+      const S* Sg = tf + h.lo * tv.r[0];  // S[t][c] = Sg[t * r_1 + c]
       S* sl = reinterpret_cast<S*>(h.slice);
       const int nr0 = h.nr0, lds = odd_ld(nr0);
-      for (int idx = lane; idx < ell * nr0; idx += nt) {
-        const int t = idx / nr0, c = idx % nr0;
-        sl[t * lds + c] = tf[(h.lo + t) * tv.r[0] + c];
-      }
-      G::sync();
       const long long c0 = clock64();
-      householder_qr<G, S>(sl, ell, nr0, lds, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
+      const bool chol = ell >= 2 * nr0 && cholesky_qr(Sg, tv.r[0], ell, nr0, sl, lds);
+      if (!chol) {  // Householder: S copied to the slice buffer, reflectors below R
+        for (int idx = lane; idx < ell * nr0; idx += nt) {
+          const int t = idx / nr0, c = idx % nr0;
+          sl[t * lds + c] = Sg[t * tv.r[0] + c];
+        }
+        G::sync();
+        householder_qr<G, S>(sl, ell, nr0, lds, reinterpret_cast<S*>(h.stau), sm.sc, sm.red, sm.wbuf);
+      }
+      if (lane == 0) const_cast<HitRec&>(h).chol = chol ? 1 : 0;
       qr_cyc += clock64() - c0;
       int tot = 1;
       for (int n = 0; n < p; ++n) {
@@ -721,6 +809,22 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     if (!h.partial) {
       const S* tf = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride + h.lo * tv.r[0];
       gemm<G, S>(ell, ro[0], h.q[0], tf, tv.r[0], 1, Ci, ro[0], 1, Y, ld0, 1, false);
+    } else if (h.chol) {
+      // Q [C_i; 0] = S R^{-1}[:, :q] C_i = S[:, :q] M with M = R[:q, :q]^{-1} C_i
+      // (R upper triangular): back substitution, one column of C_i per thread
+      const int q0 = h.q[0], lds = odd_ld(h.nr0);
+      const S* R = reinterpret_cast<const S*>(h.slice);
+      S* M = cx.W;
+      for (int c = lane; c < ro[0]; c += nt) {
+        for (int a = q0 - 1; a >= 0; --a) {
+          S v = Ci[a * ro[0] + c];
+          for (int b = a + 1; b < q0; ++b) v -= R[a * lds + b] * M[b * ro[0] + c];
+          M[a * ro[0] + c] = v / R[a * lds + a];
+        }
+      }
+      G::sync();
+      const S* Sg = reinterpret_cast<const S*>(tv.tfac) + h.level * tv.tfac_level_stride + h.lo * tv.r[0];
+      gemm<G, S>(ell, ro[0], q0, Sg, tv.r[0], 1, M, ro[0], 1, Y, ld0, 1, false);
     } else {
       for (int idx = lane; idx < ell * ro[0]; idx += nt) {
         const int t = idx / ro[0], a = idx % ro[0];
