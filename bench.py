@@ -341,6 +341,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="answer only the workload's first N queries per step (0: all; for profiling runs)")
+    ap.add_argument("--large", type=int, default=1,
+                    help="1: run the large-series section (500x500xT=8192, ranks 20, leaf 32); 0: skip")
+    ap.add_argument("--large-only", action="store_true", help="run only the large-series section and print it")
     ap.add_argument("--eig64-steps", type=int, default=2,
                     help="timed launches of the headline batch with FP64 stitch eigenproblems (0: skip)")
     ap.add_argument("--plain-steps", type=int, default=5,
@@ -377,6 +380,10 @@ def main():
     if args.p_sweep:
         torch.cuda.set_device(0)
         print(json.dumps({"p_sweep": p_sweep_section(tk, torch, torch.device("cuda", 0), 0)}))
+        return 0
+    if args.large_only:
+        torch.cuda.set_device(0)
+        print(json.dumps({"large_r20": large_section(tk, torch, torch.device("cuda", 0), 0)}))
         return 0
     if args.appends_only:
         torch.cuda.set_device(0)
@@ -549,6 +556,8 @@ def main():
         line["appends"] = append_section(tk, torch, dev, local, args.appends)
     if args.serve_seconds > 0:
         line["serving"] = serving_section(tk, torch, dev, local, args.serve_seconds)
+    if args.large:
+        line["large_r20"] = large_section(tk, torch, dev, local)
 
     # ---- FP64 oracle on the host cores: cpu_baseline + matched-error check -------
     if rank == 0 and not args.no_cpu_baseline:
@@ -1020,6 +1029,96 @@ def precision_variants(w, X, Q, idx, res):
                      "max_model_distance_rel": float(np.max(dd))}
         t.close()
     return out
+
+
+def large_section(tk, torch, dev, local, n_app=32, n_err=12, n_plain=10):
+    """The large series (500x500 slices, T = 8192, 8 GB in FP32, ranks 20,
+    leaf 32, noise 0.1), drawn on the device: tree build (HBM roofline of the
+    raw series read), the autotuned batch over its 2,000 log-uniform queries,
+    single-query latency, n_app single-slice appends (one of which completes
+    a leaf block of 500x500 Gram orders), and the relative error of sampled
+    answers against the data (||X - Y||^2 = ||X||^2 - 2 <X x_n U_n^T, G> +
+    ||G||^2, in FP64 on the device)."""
+    w = synth.WORKLOADS["large_r20"]
+    T = w["T"]
+    t0 = time.perf_counter()
+    X = synth.piecewise_tucker_device(T + n_app, w["dims"], w["ranks"], w["regime"], w["sigma"], w["seed"], dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    tree = tk.Tree(w["dims"], w["ranks"], leaf_slices=w["B"], max_iter=20, tol=0.01, dtype="f32", device=local,
+                   stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        tree.build(X[:T])
+    tree.sync()
+    build_s = time.perf_counter() - t0
+    raw = T * int(np.prod(w["dims"])) * 4
+    Q = synth.query_ranges(T, w["n_queries"], w["qseed"], "loguniform", w["lo"], w["hi"])
+    offsets = tree.layout(Q)
+    rd = torch.from_numpy(Q.copy()).to(dev)
+    od = torch.from_numpy(offsets).to(dev)
+    out = torch.empty(int(offsets[-1]), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        heavy, _ = tree.tune_batch(rd, od, out, reps=1)
+        ms = []
+        for k in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.query_batch(rd, od, out)
+            b.record(stream)
+            b.synchronize()
+            if k >= 1:
+                ms.append(a.elapsed_time(b))
+    batch_ms = float(np.mean(ms))
+    lat = plain_latency(tk, torch, tree, Q, dev, stream, list(range(0, len(Q), len(Q) // n_plain)), out)
+    # errors of sampled answers against the data
+    out_h, _, info = tree.query_batch_host(Q[:n_err], None, None, with_info=True)
+    offs_h = tree.layout(Q[:n_err])
+    errs = []
+    for i in range(n_err):
+        ts, te = int(Q[i][0]), int(Q[i][1])
+        G, U = tree.unpack(out_h[offs_h[i]:offs_h[i + 1]], te - ts)
+        r = list(info[i].ranks[: tree.p])
+        G = torch.from_numpy(np.float64(G[tuple(slice(0, x) for x in r)])).to(dev)
+        U = [torch.from_numpy(np.float64(u[:, :x])).to(dev) for u, x in zip(U, r)]
+        xx, xg = 0.0, 0.0
+        for c0 in range(ts, te, 256):
+            c1 = min(te, c0 + 256)
+            Xc = X[c0:c1].to(torch.float64)
+            xx += float((Xc * Xc).sum())
+            P = torch.einsum("tij,ta,ib,jc->abc", Xc, U[0][c0 - ts:c1 - ts], U[1], U[2])
+            xg += float((P * G).sum())
+        gg = float((G * G).sum())
+        errs.append(float(np.sqrt(max(0.0, xx - 2 * xg + gg) / xx)))
+    # appends: the open block fills and completes (leaf Tucker-ALS of a 32x500x500 block, then the merges)
+    app, done = [], []
+    for k in range(n_app):
+        with torch.cuda.stream(stream):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tree.append(X[tree.T])
+            b.record(stream)
+        b.synchronize()
+        (done if tree.T % w["B"] == 0 else app).append(a.elapsed_time(b))
+    arena = tree.arena_bytes()
+    tree.close()
+    del X, out
+    torch.cuda.empty_cache()
+    return {"workload": workload_desc(w, "large_r20"), "generate_s": gen_s,
+            "tree_build": {"seconds": build_s, "raw_bytes": raw, "arena_bytes": arena,
+                           "roofline": {"bound": "hbm", "achieved": raw / build_s / 1e9, "peak": hbm_peak_gbs(),
+                                        "unit": "GB/s", "frac": raw / build_s / 1e9 / hbm_peak_gbs()}},
+            "batch": {"queries": len(Q), "ms": batch_ms, "queries_per_s": len(Q) / (batch_ms / 1e3),
+                      "heavy_hits": heavy},
+            "plain": {"latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)}, "queries": len(lat),
+                      "queries_per_s": 1e3 / float(np.mean(lat))},
+            "rel_err_vs_data": {"queries": n_err, "mean": float(np.mean(errs)), "max": float(np.max(errs)),
+                                "note": "relative reconstruction error of the answers against the raw series"},
+            "appends": {"append_ms_mean": float(np.mean(app)) if app else None,
+                        "block_complete_ms": done, "count": n_app}}
 
 
 def eig64_throughput(tk, torch, dev, local, w, X, Q, steps):

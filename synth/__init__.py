@@ -20,6 +20,10 @@ adds its own noise; regimes are generated in parallel threads straight into a
 float32 array.  It stands in for the long 4-way streams of the serving runs,
 where one generator over the whole series would be too slow.
 
+Device series (``piecewise_tucker_device``): the same recipe drawn on a CUDA
+device by one seeded ``torch.Generator``, for the 8 GB large workload; the
+engine's benchmark alone uses it (no oracle comparison runs at that size).
+
 Query ranges: "uniform" draws two distinct integers of {0..T}, sorted, read
 as the half-open range [a, b); "loguniform" draws L = round(exp(U[ln lo,
 ln hi])) and t_s uniformly from {0..T-L}.
@@ -95,6 +99,37 @@ def piecewise_tucker_regimes(T, dims, ranks, regime, sigma, seed, literal_scale=
     return X
 
 
+def piecewise_tucker_device(T, dims, ranks, regime, sigma, seed, device):
+    """Seeded piecewise-Tucker series drawn on a CUDA device, in float32 (the
+    8 GB series of the large workload would take minutes on the host).  Same
+    recipe as ``piecewise_tucker`` (per regime: N(0,1) core scaled to unit
+    signal RMS, temporal and non-temporal factors as Q of Gaussian matrices,
+    then N(0, sigma^2) noise), drawn in that order per regime from one
+    ``torch.Generator`` on the device seeded with ``seed``; the values differ
+    from the NumPy generators'."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    ranks = tuple(int(r) for r in ranks)
+    p = len(ranks)
+    assert len(dims) == p - 1
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    X = torch.empty((int(T),) + dims, dtype=torch.float32, device=device)
+    letters = string.ascii_lowercase
+    core_idx, out_idx = letters[:p], letters[13:13 + p]
+    spec = core_idx + "," + ",".join(out_idx[n] + core_idx[n] for n in range(p)) + "->" + out_idx
+    for start in range(0, int(T), int(regime)):
+        l = min(int(regime), int(T) - start)
+        rr = [min(ranks[0], l)] + [min(r, d) for r, d in zip(ranks[1:], dims)]
+        core = torch.randn(tuple(rr), generator=g, device=device, dtype=torch.float64)
+        core *= float(np.sqrt(l * np.prod(dims) / np.prod(rr)))
+        facs = [torch.linalg.qr(torch.randn(m, r, generator=g, device=device, dtype=torch.float64))[0]
+                for m, r in zip((l,) + dims, rr)]
+        X[start:start + l] = torch.einsum(spec, core, *facs).to(torch.float32)
+        X[start:start + l] += sigma * torch.randn((l,) + dims, generator=g, device=device, dtype=torch.float32)
+    return X
+
+
 def query_ranges(T, n, seed, kind="uniform", lo=16, hi=None):
     """n seeded query ranges [t_s, t_e) over a series of length T."""
     rng = np.random.Generator(np.random.PCG64(int(seed)))
@@ -131,6 +166,10 @@ WORKLOADS = {
                         dtype="f32"),
     # 4-way stream grown by single-slice appends at append_hz while Poisson
     # range queries of log-uniform length (16..T) arrive at query_hz.
+    # Large series: 500x500 slices, T = 8192 (8 GB in FP32), ranks 20, leaf 32,
+    # noise 0.1, drawn on the device; log-uniform queries.
+    "large_r20": dict(T=8192, dims=(500, 500), ranks=(20, 20, 20), regime=512, sigma=0.1, B=32,
+                      n_queries=2000, kind="loguniform", lo=16, hi=8192, seed=1005, qseed=2005, dtype="f32"),
     "serving_4way": dict(T0=1024, T_end=16384, dims=(64, 64, 32), ranks=(8, 8, 8, 8), regime=512, sigma=0.05,
                          B=16, append_hz=1000.0, query_hz=5000.0, lo=16, seed=1004, qseed=2004, dtype="f32"),
 }
