@@ -41,9 +41,10 @@ UNIT = "queries/s"
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128   # FP32 FMA units per SM (Blackwell)
 # DRAM bytes (read + write) of one k_batch launch answering the 10,000-query
-# batch, from one ncu capture of the current kernel (None: not yet captured
-# for this kernel version).
-BATCH_DRAM_BYTES = None
+# batch: one ncu capture of the current kernel on the workload's first 1000
+# queries (123.3 MB read + 217.6 MB written, profiles/k_batch_batched_r16_full.md)
+# scaled by the queries (None: not yet captured for this kernel version).
+BATCH_DRAM_BYTES = 10 * (123.31e6 + 217.61e6)
 ORACLE_T = 1024           # the CPU oracle's tree covers the first 1024 slices
 
 
@@ -341,6 +342,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--queries", type=int, default=0,
                     help="answer only the workload's first N queries per step (0: all; for profiling runs)")
+    ap.add_argument("--heavy-hits", type=int, default=0,
+                    help="batch heavy-query threshold of the headline (0: autotuned before the warm-up)")
     ap.add_argument("--large", type=int, default=1,
                     help="1: run the large-series section (500x500xT=8192, ranks 20, leaf 32); 0: skip")
     ap.add_argument("--large-only", action="store_true", help="run only the large-series section and print it")
@@ -427,7 +430,12 @@ def main():
     # autotuner on this batch before the warm-up (untimed)
     default_heavy = tree.heavy_hits
     tt0 = time.perf_counter()
-    heavy, tune_ms = tree.tune_batch(ranges_d, offsets_d, out_d, reps=1)
+    if args.heavy_hits > 0:  # set, not tuned (profiling runs: no tuning launches)
+        tree.heavy_hits = args.heavy_hits
+        heavy, tune_ms = tree.heavy_hits, None
+    else:
+        with torch.cuda.stream(stream):
+            heavy, tune_ms = tree.tune_batch(ranges_d, offsets_d, out_d, reps=1)
     tune_s = time.perf_counter() - tt0
 
     def step():
@@ -499,8 +507,9 @@ def main():
     out_bytes = int(offsets[-1]) * 4
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": BATCH_DRAM_BYTES,
-                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (ncu); "
-                                "null: no capture of this kernel version",
+                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (ncu), "
+                                "captured on the first 1000 queries and scaled by 10 (traffic grows with the "
+                                "queries: output and per-query workspace); null: no capture of this kernel version",
                 "kernel": "k_batch<float> (one persistent launch answers the whole batch, after k_plan)",
                 "flops_per_launch": flops,
                 "peak_note": f"FP32 CUDA-core peak from unit counts: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 "
