@@ -15,5 +15,6 @@ tree     Section 4.2 + Algorithms 3/4 (Insert/Append): the stream segment tree,
 stitch   Eq. (partial-tucker) and Algorithm 2 (Stitch), Section 5.2, with the
          matricizations of Eq. (stitch-temp-2) and Eq. (stitch-nontemp-3).
 metrics  Section 8.1: reconstruction error and the relative-error metric.
+rng      the seeded random start of Algorithm 2 (splitmix64, Box-Muller, QR).
 """
-from . import tensor, hooi, tree, stitch, metrics  # noqa: F401
+from . import tensor, hooi, tree, stitch, metrics, rng  # noqa: F401

@@ -10,10 +10,11 @@ V[0] (temporal, l x q_1, orthonormal columns) and V[n] (D_n x q_n, orthonormal).
 Readings of what the paper leaves open:
   * the offsets t_i of Algorithm 2 are prefix sums of the CLIPPED lengths
     |[T_s,T_e) cap [sigma_v, tau_v)|, so that t_s = L;
-  * "randomly initialize U^(2..p)" is replaced by the implicit HOSVD of the
-    stitched tensor: U^(n) = leading eigenvectors of
+  * "randomly initialize U^(2..p)" is replaced by default by the implicit
+    HOSVD of the stitched tensor: U^(n) = leading eigenvectors of
     sum_i V_i^(n) mat_n(H_i) mat_n(H_i)^T V_i^(n)T  (= mat_n(Y~) mat_n(Y~)^T
-    because every V_i^(m) has orthonormal columns);
+    because every V_i^(m) has orthonormal columns); init="random" draws them
+    from the seeded counter-based generator of ``rng`` instead;
   * "reshape Z^(p) into r_1 x ... x r_{p-1} x D_p" is read as folding Z^(p) as
     the mode-p matricization, so G = fold_p(U^(p)T Z^(p)) = Y~ x_n U^(n)T;
   * the stopping quantity is e = sqrt(max(0, 1 - ||G||^2/||Y~||^2)) with
@@ -26,6 +27,7 @@ import numpy as np
 
 from .tensor import unfold, fold, mode_product, frob, leading_left_singular_vectors
 from .hooi import stop_error
+from .rng import seeded_factors
 
 
 def partial_hit(H, V, row_lo, row_hi):
@@ -117,10 +119,12 @@ def nontemporal_matricization(hits, U, n, offsets):
     return Z
 
 
-def stitch(hits, ranks, max_iter=20, tol=0.01):
+def stitch(hits, ranks, max_iter=20, tol=0.01, init="hosvd", seed=0):
     """Algorithm 2 (Stitch) on the hit decompositions, in time order.
 
     ``ranks`` must already be the output ranks (see ``stitched_ranks``).
+    init: "hosvd" (the implicit HOSVD start) or "random" (Algorithm 2's
+    random U^(2..p), drawn by ``rng.seeded_factors`` from ``seed``).
     Returns (G, U, iters, errs).
     """
     p = len(ranks)
@@ -132,7 +136,12 @@ def stitch(hits, ranks, max_iter=20, tol=0.01):
     for l in lengths:
         offsets.append(offsets[-1] + l)
     ynorm2 = sum(frob(H) ** 2 for H, _ in hits)
-    U = init_factors(hits, r)
+    if init == "random":
+        U = seeded_factors([hits[0][1][n].shape[0] for n in range(1, p)], r, seed)
+    elif init == "hosvd":
+        U = init_factors(hits, r)
+    else:
+        raise ValueError(init)
     e_prev = np.inf
     errs = []
     G = None

@@ -48,7 +48,7 @@ class Node:
 class StreamSegmentTree:
     """Algorithms 3/4 over leaf blocks of ``B`` slices, payloads in FP64."""
 
-    def __init__(self, dims, ranks, B=1, theta=(7, 10), max_iter=20, tol=0.01):
+    def __init__(self, dims, ranks, B=1, theta=(7, 10), max_iter=20, tol=0.01, init="hosvd", seed=0):
         self.dims = tuple(int(d) for d in dims)      # D_2..D_p
         self.ranks = tuple(int(r) for r in ranks)    # r_1..r_p (build ranks)
         self.p = len(self.ranks)
@@ -57,6 +57,8 @@ class StreamSegmentTree:
         self.theta = (int(theta[0]), int(theta[1]))
         self.max_iter = int(max_iter)
         self.tol = float(tol)
+        self.init = init           # Stitch start: "hosvd" or "random" (seeded, rng)
+        self.seed = int(seed)
         self.T = 0                 # timespan in slices
         self.root = None
         self.tail = []             # raw slices of the open block
@@ -89,7 +91,7 @@ class StreamSegmentTree:
             u1, u2 = v.left, v.right
             hits = [(u1.H, u1.V), (u2.H, u2.V)]
             r = stitched_ranks(hits, self.dims, self.ranks)
-            G, U, _, _ = stitch(hits, r, self.max_iter, self.tol)
+            G, U, _, _ = stitch(hits, r, self.max_iter, self.tol, self.init, self.seed)
             v.H, v.V = G, U
             v.kind = 'M'
             self.stitch_count += 1
@@ -196,7 +198,7 @@ class StreamSegmentTree:
         hits = self.hit_decompositions(ts, te)
         r = stitched_ranks(hits, self.dims, req)
         G, U, it, errs = stitch(hits, r, self.max_iter if max_iter is None else max_iter,
-                                self.tol if tol is None else tol)
+                                self.tol if tol is None else tol, self.init, self.seed)
         return dict(G=G, U=U, ranks=r, iters=it, errs=errs, hits=self.hit_records(ts, te))
 
     # ----- introspection for invariants -----------------------------------
