@@ -25,7 +25,7 @@ class _Structural(StreamSegmentTree):
 @pytest.fixture(autouse=True)
 def _no_payload_arithmetic(monkeypatch):
     import oracle.tree as ot
-    monkeypatch.setattr(ot, "stitch", lambda hits, r, max_iter, tol: (None, None, 0, []))
+    monkeypatch.setattr(ot, "stitch", lambda hits, r, max_iter, tol, *start: (None, None, 0, []))
     monkeypatch.setattr(ot, "stitched_ranks", lambda hits, dims, ranks: None)
 
 
