@@ -68,6 +68,20 @@ typedef enum tk_dtype { TK_F64 = 0, TK_F32 = 1 } tk_dtype;
 typedef enum tk_math { TK_MATH_AUTO = 0, TK_MATH_CUDA_CORES = 1, TK_MATH_TF32 = 2 } tk_math;
 typedef enum tk_io { TK_IO_DEVICE = 0, TK_IO_HOST = 1 } tk_io;
 
+/* Start of Stitch (Algorithm 2), for queries and node merges alike:
+ *   TK_INIT_HOSVD   the implicit HOSVD of the stitched tensor (default;
+ *                   deterministic, no random numbers);
+ *   TK_INIT_RANDOM  the paper's random U^(2..p), drawn from tk_config.seed by
+ *                   a counter-based generator: splitmix64 outputs
+ *                   mix(seed + (k+1) * 0x9E3779B97F4A7C15), uniforms
+ *                   ((out >> 11) + 1) * 2^-53, Box-Muller Gaussians (even
+ *                   element: cos, odd: sin), mode n = 2..p a D_n x r_n
+ *                   row-major matrix from element sum_{m<n} D_m r_m on (r the
+ *                   stitch's output ranks), orthonormalized by QR.  The same
+ *                   seed serves every stitch, so answers are reproducible.
+ * The leaf blocks' Tucker-ALS always starts from the HOSVD of the block. */
+typedef enum tk_init { TK_INIT_HOSVD = 0, TK_INIT_RANDOM = 1 } tk_init;
+
 /* Tree configuration.  Hyperparameter defaults follow Section 8.1 of the
  * paper: at most 20 ALS iterations, tolerance 0.01, theta = 0.7. */
 typedef struct tk_config {
@@ -87,6 +101,8 @@ typedef struct tk_config {
                                        for orders >= 20 (the tridiagonal method; smaller orders
                                        use FP32 Jacobi); 0 (default): in the tree's dtype.  FP64
                                        trees ignore it.  0 or 1. */
+  uint64_t seed;                    /* seed of TK_INIT_RANDOM */
+  int32_t init;                     /* tk_init of Stitch (default TK_INIT_HOSVD) */
 } tk_config;
 
 /* One node of a hit set (Algorithm 1, Section 5.1), in time order. */

@@ -17,6 +17,7 @@ MAX_MODES = 8
 
 TK_F64, TK_F32 = 0, 1
 MATH = {"auto": 0, "cuda_cores": 1, "tf32": 2}
+INIT = {"hosvd": 0, "random": 1}
 TK_IO_DEVICE, TK_IO_HOST = 0, 1
 
 _ERR = {
@@ -34,7 +35,7 @@ class TkConfig(ctypes.Structure):
                 ("theta_num", ctypes.c_int32), ("theta_den", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double), ("dtype", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("hbm_budget", ctypes.c_int64), ("math", ctypes.c_int32),
-                ("eig_fp64", ctypes.c_int32)]
+                ("eig_fp64", ctypes.c_int32), ("seed", ctypes.c_uint64), ("init", ctypes.c_int32)]
 
 
 class TkHit(ctypes.Structure):
@@ -187,11 +188,12 @@ class Tree:
     fraction (num, den), dtype "f64" or "f32", hbm_budget the device bytes the
     tree may hold (0: no limit), math the arithmetic of the leaf Grams ("auto":
     split-TF32 tensor cores for FP32 trees, "cuda_cores", or "tf32"), eig_fp64
-    whether an FP32 tree solves its stitch eigenproblems in FP64.
+    whether an FP32 tree solves its stitch eigenproblems in FP64, init the
+    start of Stitch ("hosvd", or "random" drawn from seed).
     """
 
     def __init__(self, dims, ranks, leaf_slices=1, theta=(7, 10), max_iter=20, tol=0.01, dtype="f32",
-                 device=0, stream=None, hbm_budget=0, math="auto", eig_fp64=False):
+                 device=0, stream=None, hbm_budget=0, math="auto", eig_fp64=False, init="hosvd", seed=0):
         self.dims = tuple(int(d) for d in dims)
         self.ranks = tuple(int(r) for r in ranks)
         self.p = len(self.ranks)
@@ -215,6 +217,10 @@ class Tree:
         cfg.hbm_budget = int(hbm_budget)
         cfg.math = MATH[math]
         cfg.eig_fp64 = 1 if eig_fp64 else 0
+        if init not in INIT:
+            raise ValueError(f"init must be one of {sorted(INIT)}")
+        cfg.init = INIT[init]
+        cfg.seed = int(seed) & ((1 << 64) - 1)
         self.cfg = cfg
         h = ctypes.c_void_p()
         s = ctypes.c_void_p(stream.cuda_stream) if stream is not None else ctypes.c_void_p()

@@ -431,6 +431,57 @@ __device__ void householder_apply_q(const S* A, int m, int kmax, int lda, const 
 }
 
 // Scratch of jacobi_eig for order n: the round-robin schedule and rotations.
+// Y (m x ncols, leading dimension ldy) <- H_{k-1} ... H_1 H_0 Y: the transpose
+// of householder_apply_q's product (Q^T Y for the Q of householder_qr).
+template <class G, class S>
+__device__ void householder_apply_qt(const S* A, int m, int kmax, int lda, const S* tau, S* Y, int ncols,
+                                     int64_t ldy, S* wbuf = nullptr) {
+  const int lane = G::rank() & 31, warp = G::rank() >> 5, nw = G::nwarps();
+  if (wbuf && G::nwarps() > 1 && m >= 2 * G::size()) {
+    for (int j = 0; j < kmax; ++j)
+      if (tau[j] != S(0)) reflect_cols<G, S>(A, lda, j, j, m, tau[j], Y, ldy, ncols, wbuf);
+    return;
+  }
+  for (int j = 0; j < kmax; ++j) {
+    const S t = tau[j];
+    if (t == S(0)) continue;
+    for (int c = warp; c < ncols; c += nw) {
+      S w = 0;
+      for (int i = j + 1 + lane; i < m; i += 32) w += A[i * lda + j] * Y[i * ldy + c];
+      w = warp_sum(w);
+      w = (w + Y[j * ldy + c]) * t;
+      __syncwarp();
+      if (lane == 0) Y[j * ldy + c] -= w;
+      for (int i = j + 1 + lane; i < m; i += 32) Y[i * ldy + c] -= w * A[i * lda + j];
+    }
+    G::sync();
+  }
+}
+
+// Counter-based Gaussians for the seeded start of Stitch.  splitmix64
+// (Steele, Lea and Flood, OOPSLA 2014; the finalizer constants of Vigna's
+// public-domain reference): output k of the stream seeded with s is
+// mix(s + (k + 1) * 0x9E3779B97F4A7C15).  Uniform k = ((output k >> 11) + 1)
+// * 2^-53 in (0, 1].  Gaussian e by Box-Muller (1958) on uniforms 2(e/2) and
+// 2(e/2) + 1: sqrt(-2 ln u1) cos(2 pi u2) for even e, sin for odd e.  Every
+// value depends only on (s, e), so any thread computes any element.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t k) {
+  uint64_t z = s + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double uniform_at(uint64_t s, uint64_t k) {
+  return (double)((splitmix64_at(s, k) >> 11) + 1) * 0x1.0p-53;
+}
+__device__ __forceinline__ double gaussian_at(uint64_t s, uint64_t e) {
+  const uint64_t j = e >> 1;
+  const double u1 = uniform_at(s, 2 * j), u2 = uniform_at(s, 2 * j + 1);
+  const double rad = sqrt(-2.0 * log(u1));
+  const double ang = 2.0 * 3.141592653589793 * u2;
+  return rad * ((e & 1) ? sin(ang) : cos(ang));
+}
+
 template <class S> struct JacobiScratch {
   int* pq;    // >= n/2 + 1
   S* c;       // >= n/2 + 1

@@ -159,6 +159,8 @@ TkTreeView make_view(const tk_tree* t) {
   v.max_iter = t->cfg.max_iter;
   v.tol = t->cfg.tol;
   v.eig64 = (t->cfg.eig_fp64 && t->cfg.dtype == TK_F32) ? 1 : 0;
+  v.init = t->cfg.init;
+  v.seed = t->cfg.seed;
   v.T = t->T;
   v.nb = t->nb;
   v.nbt = nbt_of(t);
@@ -318,6 +320,11 @@ int64_t stitch_ws_bound(const tk_tree* t, int hmax) {
   int rmax = 1;
   for (int n = 0; n < p; ++n) rmax = std::max(rmax, r[n]);
   tot += round32(tk::trd_scratch_elems((int)neig, rmax, 32));
+  if (t->cfg.init == TK_INIT_RANDOM) {  // the random start's Gaussian matrix, its Q, and tau
+    int64_t dr = 0;
+    for (int n = 1; n < p; ++n) dr = std::max<int64_t>(dr, t->cfg.dims[n] * (r[n] + 1));
+    tot += 2 * round32(dr) + round32(rmax);
+  }
   if (t->cfg.eig_fp64 && t->cfg.dtype == TK_F32)  // the FP64 eigenproblem's buffers, in float units
     tot += 2 * (round32(neig * neig) + round32(neig * rmax) + round32(tk::trd_scratch_elems((int)neig, rmax, 32)) + 32);
   return tot + 256;
@@ -681,6 +688,7 @@ int tk_tree_create(const tk_config* cfg, void* cuda_stream, tk_tree** out) {
   if (cfg->max_iter < 1 || (cfg->dtype != TK_F64 && cfg->dtype != TK_F32)) return TK_ERR_ARG;
   if (cfg->hbm_budget < 0) return TK_ERR_ARG;
   if (cfg->eig_fp64 != 0 && cfg->eig_fp64 != 1) return TK_ERR_ARG;
+  if (cfg->init != TK_INIT_HOSVD && cfg->init != TK_INIT_RANDOM) return TK_ERR_ARG;
   if (cfg->math < TK_MATH_AUTO || cfg->math > TK_MATH_TF32 || (cfg->math == TK_MATH_TF32 && cfg->dtype != TK_F32))
     return TK_ERR_ARG;
   for (int n = 0; n < cfg->p; ++n)
@@ -1216,7 +1224,7 @@ extern "C" int tk_range_query_batch_noalloc(tk_tree* t, int n, const int64_t* ra
 // and layout, and copying the bytes back restores the tree exactly.
 namespace {
 
-constexpr char kFileMagic[8] = {'T', 'K', 'T', 'R', 'E', 'E', '\0', '\2'};
+constexpr char kFileMagic[8] = {'T', 'K', 'T', 'R', 'E', 'E', '\0', '\3'};
 constexpr int kFileSections = 4 + TK_MAXP;
 
 struct TkFileHeader {

@@ -28,6 +28,8 @@ struct TkTreeView {
   int max_iter;
   double tol;
   int eig64;               // FP32 tree: stitch eigenproblems (tridiagonal method) in FP64
+  int init;                // Stitch start: TK_INIT_HOSVD or TK_INIT_RANDOM (seeded)
+  uint64_t seed;
   int64_t T, nb, nbt;      // slices, complete blocks, blocks incl. the tail
   int height;              // ceil(log2 nbt) + 1, 0 when empty
   int nlevels;

@@ -70,9 +70,11 @@ template <class S> struct StitchCtx {
   S *phi[TK_MAXP], *tau[TK_MAXP], *R[TK_MAXP], *E[TK_MAXP], *Vs[TK_MAXP];
   S *K, *b0, *b1, *N, *W, *G, *T, *A, *V, *w, *cs, *trdv;
   double *Ad, *Ed, *trdd, *scd;  // FP64 eigenproblem of an FP32 tree (eig64)
+  S *Ug, *Uq, *Ut;               // seeded start: Gaussian matrix (its QR), its Q, tau
   int* pq;
   int neig;           // largest eig order of the job
   int smem_used;      // bytes of the shared arena in use
+  int stage_end;      // arena offset of the first buffer after the staging region (E and later)
 };
 
 // Shared memory of one job group (a warp or a CTA): this header, then the
@@ -399,6 +401,7 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       if (v > wmax) wmax = v;
     }
     cx.W = take(wmax);
+    cx.stage_end = (int)scur;  // everything from here on may be live while Phi_n is staged
     for (int n = 0; n < p; ++n) cx.E[n] = take((int64_t)cx.c[n] * cx.ro[n]);
     for (int n = 1; n < p; ++n) cx.R[n] = take((int64_t)cx.c[n] * cx.k[n]);
     for (int i = 0; i < cx.nh; ++i) {
@@ -423,6 +426,19 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
       } else {
         h.slice = h.stau = nullptr;
       }
+    }
+    cx.Ug = cx.Uq = cx.Ut = nullptr;
+    if (tv.init == TK_INIT_RANDOM) {
+      int64_t dr = 0;
+      int rmx = 1;
+      for (int n = 1; n < p; ++n) {
+        const int64_t v = (int64_t)tv.D[n] * odd_ld(cx.ro[n]);
+        dr = v > dr ? v : dr;
+        rmx = cx.ro[n] > rmx ? cx.ro[n] : rmx;
+      }
+      cx.Ug = take(dr);
+      cx.Uq = take(dr);
+      cx.Ut = take(rmx);
     }
     cx.smem_used = (int)scur;
     if (cur > ws_cap && cx.err == 0) cx.err = TK_DEV_ERR_WORKSPACE;
@@ -651,8 +667,9 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
   // so Phi_n, when it lives in global memory, is worked on there.
   auto staging = [&](int64_t nel) -> S* {
     if (!__isShared(cx.A) || __isShared(cx.phi[1])) return nullptr;
-    const char* lim = __isShared(cx.E[0]) ? reinterpret_cast<const char*>(cx.E[0])
-                                          : reinterpret_cast<const char*>(arena + arena_bytes);
+    // up to where E was carved: buffers taken after it (tau, R, the cores)
+    // may sit in the arena's tail even when E itself went to global memory
+    const char* lim = reinterpret_cast<const char*>(arena + cx.stage_end);
     return (lim - reinterpret_cast<const char*>(cx.A)) >= (int64_t)(nel * sizeof(S)) ? cx.A : nullptr;
   };
 
@@ -683,6 +700,30 @@ __device__ void stitch_job(const TkTreeView& tv, const TkEpoch& ep, int mode, in
     if (stg) {  // the reflectors are needed again for the output
       for (int idx = lane; idx < Dn * ldp; idx += nt) cx.phi[n][idx] = stg[idx];
       G::sync();
+    }
+    if (tv.init == TK_INIT_RANDOM) {
+      // Algorithm 2's random start: U^(n) = Q of a seeded D_n x r_n Gaussian
+      // matrix (elements from sum_{m<n} D_m r_m on), entering the coefficient
+      // space as E_n = Q_n^T U^(n) (first c_n rows of H_{c-1}..H_0 U^(n)):
+      // W_im = U^(m)T V~_i^(m) = E_m^T R_m[:, blk i] holds for any U^(m)
+      const int rn = cx.ro[n], ldu = odd_ld(rn);
+      int64_t off = 0;
+      for (int m = 1; m < n; ++m) off += (int64_t)tv.D[m] * cx.ro[m];
+      for (int idx = lane; idx < Dn * rn; idx += nt) {
+        const int d = idx / rn, c = idx - (idx / rn) * rn;
+        cx.Ug[d * ldu + c] = (S)gaussian_at(tv.seed, (uint64_t)(off + idx));
+        cx.Uq[d * ldu + c] = d == c ? S(1) : S(0);
+      }
+      G::sync();
+      householder_qr<G, S>(cx.Ug, Dn, rn, ldu, cx.Ut, sm.sc, sm.red, sm.wbuf);
+      householder_apply_q<G, S>(cx.Ug, Dn, rn < Dn ? rn : Dn, ldu, cx.Ut, cx.Uq, rn, ldu, sm.wbuf);
+      householder_apply_qt<G, S>(cx.phi[n], Dn, cn, ldp, cx.tau[n], cx.Uq, rn, ldu, sm.wbuf);
+      for (int idx = lane; idx < cn * rn; idx += nt) {
+        const int a = idx / rn, b = idx - (idx / rn) * rn;
+        cx.E[n][idx] = cx.Uq[a * ldu + b];
+      }
+      G::sync();
+      continue;
     }
     for (int idx = lane; idx < cn * cn; idx += nt) A[idx] = 0;
     G::sync();

@@ -47,7 +47,7 @@ def test_defaults_follow_the_paper(lib):
                                  dict(theta_den=0), dict(theta_num=0), dict(max_iter=0), dict(dtype=5),
                                  dict(ranks0=0), dict(ranks0=5000), dict(dims1=0), dict(hbm_budget=-1),
                                  dict(math=-1), dict(math=3), dict(math=2, dtype=0),
-                                 dict(eig_fp64=2), dict(eig_fp64=-1)])
+                                 dict(eig_fp64=2), dict(eig_fp64=-1), dict(init=2), dict(init=-1)])
 def test_invalid_configurations_are_rejected(lib, bad):
     c = _cfg(lib, **bad)
     h = ctypes.c_void_p(1234)
@@ -111,7 +111,7 @@ class _FileHeader(ctypes.Structure):
                 ("sec_bytes", ctypes.c_int64 * (4 + tk.MAX_MODES))]
 
 
-def _header(lib, magic=b"TKTREE\x00\x02", **kw):
+def _header(lib, magic=b"TKTREE\x00\x03", **kw):
     h = _FileHeader()
     h.header_bytes = ctypes.sizeof(_FileHeader)
     h.cfg = _cfg(lib, leaf_slices=4)
@@ -136,7 +136,7 @@ def test_files_that_are_not_tree_files_are_rejected(lib, tmp_path):
     f = tmp_path / "bad.tkt"
     good = _header(lib)
     bad = [b"", b"not a tree file", good[:40],                      # empty, garbage, truncated header
-           _header(lib, magic=b"TKTREE\x00\x01"),                  # another format version
+           _header(lib, magic=b"TKTREE\x00\x02"),                  # another format version
            _header(lib, header_bytes=8), _header(lib, nsec=3),       # another header layout
            _header(lib, elem_bytes=8),                               # element size not the dtype's
            _header(lib, nb=11),                                      # nb != T / B
