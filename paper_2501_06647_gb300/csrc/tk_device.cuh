@@ -478,8 +478,9 @@ __device__ __forceinline__ double gaussian_at(uint64_t s, uint64_t e) {
   const uint64_t j = e >> 1;
   const double u1 = uniform_at(s, 2 * j), u2 = uniform_at(s, 2 * j + 1);
   const double rad = sqrt(-2.0 * log(u1));
-  const double ang = 2.0 * 3.141592653589793 * u2;
-  return rad * ((e & 1) ? sin(ang) : cos(ang));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);  // sin and cos of 2 pi u2, the argument reduced exactly
+  return rad * ((e & 1) ? sn : cs);
 }
 
 template <class S> struct JacobiScratch {
