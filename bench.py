@@ -533,8 +533,9 @@ def main():
                    "heavy_hits": heavy,
                    "autotune": {"chosen_heavy_hits": heavy, "default_heavy_hits": default_heavy,
                                 "best_ms": tune_ms, "seconds": tune_s,
-                                "note": "tk_batch_tune: each candidate threshold timed once on this batch "
-                                        "before the warm-up"}},
+                                "note": ("set by --heavy-hits (no tuning)" if args.heavy_hits > 0 else
+                                         "tk_batch_tune: each candidate threshold timed once on this batch "
+                                         "before the warm-up")}},
         "latency_ms": {"p50": pct(done_ms, 50), "p99": pct(done_ms, 99),
                        "mode": "in-batch: batch launch to each query's completion (GPU global timer), "
                                f"{n_q} concurrent queries",
