@@ -80,3 +80,10 @@ def test_build_and_append_check_device_tensors():
         t.build(FakeCuda((16, 5, 7), "float64"))              # slices of the wrong shape
     with pytest.raises(ValueError):
         t.append(FakeCuda((7, 5), "float64", device=2))
+
+
+def test_start_of_stitch_is_checked_before_creation():
+    # an unknown start raises before the library creates anything (no GPU needed)
+    with pytest.raises(ValueError):
+        tk.Tree((7, 5), (3, 3, 3), leaf_slices=4, init="hosvd-ish")
+    assert tk.INIT == {"hosvd": 0, "random": 1}
