@@ -94,3 +94,59 @@ def test_random_and_hosvd_starts_differ_only_in_the_start():
     with pytest.raises(ValueError):
         st.stitch([(np.ones((1, 1, 1)), [np.ones((1, 1)), np.ones((8, 1)), np.ones((7, 1))])], [1, 1, 1],
                   init="bogus")
+
+
+def _mode_product(X, M, n):
+    return np.moveaxis(np.tensordot(M, X, axes=(1, n)), 0, n)
+
+
+def _dense_hooi_from(Y, r, U0, iters):
+    """Textbook HOOI (Gauss-Seidel over the modes) on the dense tensor Y from
+    the start U0 (U0[0] unused: the temporal factor is updated first),
+    written with NumPy's SVD, independently of the oracle's stitch code."""
+    p = Y.ndim
+    U = list(U0)
+    for _ in range(iters):
+        for n in range(p):
+            Z = Y
+            for m in range(p):
+                if m != n:
+                    Z = _mode_product(Z, U[m].T, m)
+            Zn = np.moveaxis(Z, n, 0).reshape(Z.shape[n], -1)
+            u, _, _ = np.linalg.svd(Zn, full_matrices=False)
+            U[n] = u[:, : r[n]]
+    G = Y
+    for m in range(p):
+        G = _mode_product(G, U[m].T, m)
+    return G, U
+
+
+@pytest.mark.parametrize("iters", [1, 3])
+def test_random_start_stitch_equals_dense_hooi_from_the_same_start(iters):
+    # Algorithm 2 from the seeded start is HOOI on the stitched tensor Y~ from
+    # the same U^(2..p): the literal matricizations of the oracle's Stitch
+    # against a dense HOOI loop on the materialized Y~
+    rs = np.random.default_rng(5)
+    dims, q = (9, 8), (3, 3, 3)
+    hits = []
+    for ell in (6, 4, 5):
+        H = rs.standard_normal(q)
+        V = [np.linalg.qr(rs.standard_normal((ell, q[0])))[0]] + \
+            [np.linalg.qr(rs.standard_normal((d, k)))[0] for d, k in zip(dims, q[1:])]
+        hits.append((H, V))
+    Y = st.materialize_stitched(hits)
+    r = st.stitched_ranks(hits, dims, (4, 3, 3))
+    G, U, it, _ = st.stitch(hits, r, max_iter=iters, tol=0, init="random", seed=21)
+    Gd, Ud = _dense_hooi_from(Y, r, rng.seeded_factors(dims, r, 21), iters)
+    Ya, Yb = G, Gd
+    for m in range(3):
+        Ya, Yb = _mode_product(Ya, U[m], m), _mode_product(Yb, Ud[m], m)
+    assert it == iters
+    assert np.linalg.norm(Ya - Yb) < 1e-10 * np.linalg.norm(Y)
+    # and differs from the HOSVD start after one iteration
+    if iters == 1:
+        Gh, Uh, _, _ = st.stitch(hits, r, max_iter=1, tol=0)
+        Yh = Gh
+        for m in range(3):
+            Yh = _mode_product(Yh, Uh[m], m)
+        assert np.linalg.norm(Ya - Yh) > 1e-6 * np.linalg.norm(Y)
